@@ -1,0 +1,355 @@
+#!/usr/bin/env python
+"""Benchmark of the DID sweep on one GB300 (or N independent replicas).
+
+A step is one sweep: for k = 1..K the b_k update (grid reduction of R c_k^T),
+the c_k update fused with the residual write-back, the objective of the
+sweep, and -- at the workload's cadence -- the dense refresh R = X - B C.
+
+Prints one JSON line (rank 0).  `value` is sweeps/s summed over ranks, timed
+with CUDA events on the library's stream between barriers; `roofline` is the
+sweep kernel's algorithmic HBM bytes over its own CUDA-event time against the
+measured copy bandwidth; `e2e` is the same metric through the public API from
+pinned host memory (X uploaded, factors read back, inside the timed region);
+`cpu_baseline` is the FP64 oracle on one host core over a column slice of the
+same workload, scaled linearly in N (sweep cost is O(MNK)).
+
+`--impl reference` times the oracle itself as the reference arm.
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "DID sweeps/s + HBM GB/s (BF16-R vs FP32 plain); serve solves/s, p50/p99 ms"
+
+# Workloads (synthetic, seeded; shapes of the paper's experiments).
+WORKLOADS = {
+    "planted_exp_5000x200000_k50": dict(M=5000, N=200000, K=50, gen="planted", coords=1, zero_frac=0.3,
+                                        sigma=0.05, salt_frac=0.0, refresh_every=10, init_scale=False),
+    "image_like_784x70000_k16": dict(M=784, N=70000, K=16, gen="image", refresh_every=0, init_scale=True),
+    "salt_10000x500000_k100": dict(M=10000, N=500000, K=100, gen="planted", coords=0, zero_frac=0.0,
+                                   sigma=0.0, salt_frac=0.01, refresh_every=5, init_scale=False),
+    "planted_uniform_200x1000_k10": dict(M=200, N=1000, K=10, gen="planted", coords=0, zero_frac=0.0,
+                                         sigma=0.01, salt_frac=0.0, refresh_every=0, init_scale=False),
+}
+DEFAULT_WORKLOAD = "planted_exp_5000x200000_k50"
+# Column slice of each workload for the oracle timing (about 10-20 s of CPU work).
+CPU_SAMPLE_COLS = {"planted_exp_5000x200000_k50": 1000, "image_like_784x70000_k16": 4000,
+                   "salt_10000x500000_k100": 250, "planted_uniform_200x1000_k10": 1000}
+CPU_SAMPLE_SWEEPS = 3
+
+SWEEP_SOURCES = ["paper_1802_08938_gb300/csrc/did_sweep.cu", "paper_1802_08938_gb300/csrc/did_internal.cuh"]
+
+
+def sweep_source_hash():
+    h = hashlib.sha256()
+    for p in SWEEP_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def profiled_traffic(workload, precision):
+    """DRAM bytes per sweep-kernel launch from the committed ncu summary, if it
+    was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "sweep_kernel_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get("%s/%s" % (workload, precision))
+    if not e or e.get("source_hash") != sweep_source_hash():
+        return None
+    return e.get("bytes_per_sweep")
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        smax = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": smax, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# --------------------------------------------------------------- CPU oracle
+def cpu_sample(workload, cols, sweeps):
+    """Time `sweeps` oracle sweeps on the first `cols` columns (runs in a child
+    process with one BLAS thread).  Returns seconds per sweep of the slice."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench._cpu_sample_child(%r, %d, %d)))" % (ROOT, workload, cols, sweeps))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, cwd=ROOT)
+    if r.returncode != 0:
+        raise RuntimeError("cpu sample failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def _cpu_sample_child(workload, cols, sweeps):
+    from oracle import did_oracle as O
+    from synth import workloads as SW
+    w = WORKLOADS[workload]
+    M, K = w["M"], w["K"]
+    if w["gen"] == "image":
+        X = SW.image_like(M, cols, 0)
+    else:
+        X, _, _ = SW.planted(M, cols, K, 0, coords="exp" if w["coords"] == 1 else "uniform",
+                             zero_frac=w["zero_frac"], sigma=w["sigma"], salt_frac=w["salt_frac"])
+    B, C = SW.init_factors(M, cols, K, 0)
+    if w["init_scale"]:
+        B, C = O.init_scale(X, B, C)
+    R = O.residual(X, B, C)
+    times = []
+    for _ in range(sweeps):
+        t = time.perf_counter()
+        B, C, R, _ = O.sweep_hals(X, B, C, R)
+        times.append(time.perf_counter() - t)
+    return {"sec_per_sweep": sum(times) / len(times), "times": times}
+
+
+def cpu_baseline(workload):
+    w = WORKLOADS[workload]
+    cols = min(CPU_SAMPLE_COLS[workload], w["N"])
+    r = cpu_sample(workload, cols, CPU_SAMPLE_SWEEPS)
+    sweeps_per_s = (1.0 / r["sec_per_sweep"]) * cols / w["N"]
+    return {"value": sweeps_per_s, "unit": "sweeps/s", "cores": 1, "kind": "oracle",
+            "sample": "%d FP64 oracle sweeps (NumPy, 1 thread) on the first %d of %d columns (M=%d, K=%d), "
+                      "scaled linearly in N" % (CPU_SAMPLE_SWEEPS, cols, w["N"], w["M"], w["K"])}
+
+
+# ------------------------------------------------------------------ main
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = WORKLOADS[args.workload]
+    cols = min(CPU_SAMPLE_COLS[args.workload], w["N"])
+    r = cpu_sample(args.workload, cols, args.warmup + args.steps)
+    times = r["times"][args.warmup:]
+    sec = sum(times) / len(times)
+    value = (1.0 / sec) * cols / w["N"]
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "M": w["M"], "N": w["N"], "K": w["K"],
+                                            "precision": "fp64 oracle"},
+            "cpu_baseline": {"value": value, "unit": "sweeps/s", "cores": 1, "kind": "oracle",
+                             "sample": "each step: one FP64 oracle sweep (NumPy, 1 thread) on the first %d of %d "
+                                       "columns, scaled linearly in N" % (cols, w["N"])},
+            "e2e": {"value": value, "unit": "sweeps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16r"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1802_08938_gb300 as did
+
+    w = WORKLOADS[args.workload]
+    M, N, K = w["M"], w["N"], w["K"]
+    prec = did.DID_BF16R if args.precision == "bf16r" else did.DID_FP32
+    s_bytes = 2 if prec == did.DID_BF16R else 4
+    seed = rank
+    stream = torch.cuda.current_stream()
+
+    X = torch.empty((N, M), dtype=torch.float32, device="cuda")   # M x N column-major
+    if w["gen"] == "image":
+        did.did_generate_image(X, M, N, seed, 0.8, stream=stream)
+    else:
+        did.did_generate_planted(X, M, N, K, seed, coords=w["coords"], zero_frac=w["zero_frac"],
+                                 sigma=w["sigma"], salt_frac=w["salt_frac"], salt_value=5.0, stream=stream)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    ctx = did.Context(X, M, N, K, seed=seed, precision=prec, refresh_every=w["refresh_every"],
+                      init_scale=w["init_scale"], stream=stream)
+    for _ in range(args.warmup):
+        ctx.sweep(1)
+    info0 = ctx.info()
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        ctx.sweep(1)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    info1 = ctx.info()
+    ms = ev0.elapsed_time(ev1)
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * args.steps / (ms / 1000.0)
+
+    # Roofline of the sweep kernel: algorithmic bytes / its own event time.
+    launches = info1["sweep_launches"] - info0["sweep_launches"]
+    prologues = info1["prologue_launches"] - info0["prologue_launches"]
+    kms = info1["sweep_kernel_ms"] - info0["sweep_kernel_ms"]
+    alg_bytes = args.steps * 2.0 * K * M * N * s_bytes + prologues * 1.0 * M * N * s_bytes
+    achieved = alg_bytes / (kms / 1000.0) / 1e9
+    peak, peak_kind = measured_peaks()
+    traffic = profiled_traffic(args.workload, args.precision)
+    dense_launches = info1["dense_launches"] - info0["dense_launches"]
+    gpu_launches = launches + dense_launches
+    ctx.close()
+    del ctx
+
+    e2e = None
+    if not args.no_e2e:
+        Xh = torch.empty((N, M), dtype=torch.float32, pin_memory=True)
+        Xh.copy_(X)
+        del X
+        torch.cuda.empty_cache()
+        Bh = torch.empty((K, M), dtype=torch.float32, pin_memory=True)
+        Ch = torch.empty((K, N), dtype=torch.float32, pin_memory=True)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c2 = did.Context(Xh, M, N, K, seed=seed, precision=prec, refresh_every=w["refresh_every"],
+                         init_scale=w["init_scale"], stream=stream)
+        c2.sweep(args.steps)
+        did.did_get_factors(c2.h, Bh, Ch)
+        t1 = time.perf_counter()
+        c2.close()
+        e_sec = t1 - t0
+        if ws > 1:
+            t = torch.tensor([e_sec], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e_sec = float(t.item())
+        e2e = {"value": ws * args.steps / e_sec, "unit": "sweeps/s",
+               "h2d_bytes_per_step": int(M * N * 4 / args.steps),
+               "d2h_bytes_per_step": int((M * K + K * N) * 4 / args.steps),
+               "note": "one job per run: did_create from pinned host X, %d sweeps, factors read back" % args.steps}
+    else:
+        del X
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.workload)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == did.DID_FP32 else "bf16-storage/f32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "M": M, "N": N, "K": K, "precision": args.precision,
+                       "refresh_every": w["refresh_every"], "init_scale": w["init_scale"],
+                       "l2": "inputs larger than L2 (R is %.1f GB)" % (M * N * s_bytes / 1e9),
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "sweep_kernel", "peak_kind": peak_kind,
+                         "alg_bytes_per_sweep": 2.0 * K * M * N * s_bytes,
+                         "kernel_ms_per_sweep": kms / max(1, args.steps)},
+            "e2e": e2e,
+            "gpu_launches": int(gpu_launches),
+            "cpu_baseline": cpu,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,195 @@
+/*
+ * did.h -- C ABI of the GB300 DID library: nonnegative matrix factorisation
+ * by exact rank-one block coordinate descent with an incrementally updated
+ * residual (Gao & Chu, "DID: Distributed Incremental Block Coordinate Descent
+ * for Nonnegative Matrix Factorization", AAAI 2018).
+ *
+ * Problem (Section 1, optimisation problem opt:nmf):
+ *     minimise f(B, C) = 1/2 ||X - B C||_F^2   subject to  B >= 0, C >= 0,
+ * X is M x N with one sample per column, B is M x K, C is K x N.
+ *
+ * Layouts at this boundary (all float32):
+ *   X : M x N column-major, leading dimension M (sample j is contiguous);
+ *       equivalently a row-major N x M array.
+ *   B : M x K column-major (column b_k contiguous).
+ *   C : K x N row-major (row c_k contiguous).
+ *   R : M x N column-major residual X - B C.
+ *
+ * Conventions shared by every call:
+ *   - Every call returns a did_status and never aborts the process.  A failed
+ *     call leaves the context usable, except after DID_ECUDA caused by a
+ *     sticky CUDA error (the CUDA context itself is then lost).
+ *   - Pointers marked "host or device" are classified with
+ *     cudaPointerGetAttributes; the library copies from / into them and never
+ *     keeps them.  The caller keeps ownership of every buffer it passes.
+ *   - A context owns all device memory it allocates and frees it in
+ *     did_destroy.  A context is not thread-safe; its work is ordered on the
+ *     stream given in did_options (NULL = the legacy default stream), and every
+ *     call that returns data to the host synchronises that stream.
+ */
+#ifndef DID_H
+#define DID_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Opaque factorisation context; owns all device memory it allocates. */
+typedef struct did_ctx did_ctx;
+
+typedef enum {
+    DID_OK = 0,
+    DID_PENDING = 1,        /* serving: request not finished yet */
+    DID_EINVAL = -1,        /* bad argument: sizes, NULL pointers, negative or non-finite X */
+    DID_ENOMEM = -2,        /* device allocation failed */
+    DID_ECUDA = -3,         /* a CUDA runtime call failed; see did_last_error */
+    DID_ETIMEOUT = -4,      /* a bounded device-side wait ran out; state kept consistent */
+    DID_E_TOO_LARGE = -5,   /* problem exceeds a documented size limit */
+    DID_EBUSY = -6          /* resource (slot, budget) not available now */
+} did_status;
+
+typedef enum { DID_FP32 = 0, DID_BF16R = 1 } did_precision;
+
+/* Block order of one sweep.
+ * DID_ORDER_INTERLEAVED: b_1, c_1, b_2, c_2, ..., b_K, c_K -- the rank-one
+ *   residue order of HALS (Section 2, HALS closed forms).
+ * DID_ORDER_DID: c_1..c_K then b_1..b_K -- the order of DBCD and DID
+ *   (Algorithms 2 and 3).  Both apply the same exact block minimisers. */
+typedef enum { DID_ORDER_INTERLEAVED = 0, DID_ORDER_DID = 1 } did_order;
+
+/* Stopping rule of did_factor.
+ * DID_STOP_RELCHANGE: |f_{t-1} - f_t| / f_{t-1} < tol, or f_t == 0.
+ * DID_STOP_PAPER_EPS: f_t <= tol * f_0 (Section 5: ||E^t||^2 <= eps ||E^0||^2). */
+typedef enum { DID_STOP_RELCHANGE = 0, DID_STOP_PAPER_EPS = 1 } did_stop;
+
+typedef struct {
+    int32_t precision;      /* did_precision; DID_BF16R stores R in bfloat16 */
+    int32_t order;          /* did_order */
+    int32_t refresh_every;  /* recompute R = X - B C densely before every n-th sweep; 0 = never */
+    int32_t stop;           /* did_stop */
+    int32_t init_scale;     /* 1: scale B and C by sqrt(<X,BC>/||BC||^2) after initialisation */
+    int32_t grid_ctas;      /* persistent grid size; 0 = one per SM times occupancy */
+    const float* B_init;    /* optional start point, host or device, M x K column-major; NULL = seeded */
+    const float* C_init;    /* optional start point, host or device, K x N row-major; NULL = seeded */
+    void* stream;           /* cudaStream_t to order all work on; NULL = legacy default stream */
+    uint64_t timeout_ns;    /* limit of every device-side grid wait; 0 = 4 s */
+    int32_t debug_barrier_extra; /* test hook: arrivals a grid wait expects beyond the grid (0 in use) */
+    int32_t reserved;
+} did_options;
+
+typedef struct {
+    int64_t M, N;
+    int32_t K;
+    int32_t precision, order;
+    int32_t grid_ctas;       /* persistent grid of the sweep kernel */
+    int32_t group_threads;   /* threads cooperating on one column */
+    int32_t vecs_per_thread; /* 16-byte vectors of a column each thread holds */
+    int64_t ld;              /* padded leading dimension of the device X and R */
+    int64_t sweeps_done;
+    int64_t degenerate_events; /* blocks left unchanged because a norm was exactly zero */
+    int64_t refreshes;
+    size_t device_bytes;     /* device memory owned by the context */
+    /* Device time of the library's own launches, from CUDA events recorded on
+     * the context's stream around each launch (accumulated since creation). */
+    int64_t sweep_launches;  /* persistent sweep-kernel launches */
+    int64_t prologue_launches; /* sweep launches that first re-formed R c_1^T */
+    double sweep_kernel_ms;  /* total device time of those launches */
+    int64_t dense_launches;  /* refresh / objective / scaling passes */
+    double dense_kernel_ms;
+} did_info;
+
+/* Fill *opt with the defaults: FP32, interleaved order, no refresh,
+ * relative-change stopping, no init scaling, auto grid, seeded start point,
+ * legacy default stream, 4 s wait limit. */
+void did_default_options(did_options* opt);
+
+/* Create a factorisation context for X (host or device, M x N column-major).
+ * The library copies X to the device, checks it is finite and >= 0
+ * (DID_EINVAL otherwise), draws the start point B, C uniform[0,1) from `seed`
+ * with the counter-based generator (streams 4 and 5, B[i,k] = word k*M+i,
+ * C[k,j] = word k*N+j), and forms R = X - B C.
+ * Requires 1 <= K <= min(M, N).  *out receives the context (NULL on error). */
+did_status did_create(const float* X, int64_t M, int64_t N, int32_t K, uint64_t seed,
+                      did_ctx** out);
+did_status did_create_ex(const float* X, int64_t M, int64_t N, int32_t K, uint64_t seed,
+                         const did_options* opt, did_ctx** out);
+
+/* Run n_sweeps sweeps in the context's block order.  Each b_k / c_k step is
+ * the exact nonnegative minimiser of its block (Section 2, HALS closed forms;
+ * Section 4.1, equations up:c and sol:b_i): with A = R + b_k c_k,
+ *     b_k := [A c_k^T / (c_k c_k^T)]_+ ,   c_k := [b_k^T A / (b_k^T b_k)]_+ ,
+ * and the residual is updated in place, R := A - b_k c_k (Section 4.2).
+ * A block whose partner has zero norm is left unchanged.  After each sweep
+ * 1/2 ||R||^2 is appended to the objective trace. */
+did_status did_sweep(did_ctx* ctx, int32_t n_sweeps);
+
+/* Sweep until the context's stopping rule holds with tolerance tol, or
+ * max_iter sweeps.  *iters_done and *final_obj (may be NULL) receive the
+ * sweep count of this call and the last trace value. */
+did_status did_factor(did_ctx* ctx, int32_t max_iter, double tol, int32_t* iters_done,
+                      double* final_obj);
+
+/* Exact objective 1/2 ||X - B C||_F^2 from X, B, C in a fresh pass
+ * (float32 products, float64 accumulation); R is not touched. */
+did_status did_objective(did_ctx* ctx, double* obj);
+
+/* 1/2 ||R||_F^2 of the stored residual (the last trace value). */
+did_status did_residual_objective(did_ctx* ctx, double* obj);
+
+/* Recompute R = X - B C densely (Algorithm 3 recomputes e_j := x_j - B c_j). */
+did_status did_refresh_residual(did_ctx* ctx);
+
+/* Copy B (M x K column-major) and C (K x N row-major) out; either pointer
+ * may be NULL; host or device destinations. */
+did_status did_get_factors(did_ctx* ctx, float* B, float* C);
+
+/* Replace B and C (host or device sources, same layouts; must be finite and
+ * >= 0) and recompute R.  With did_get_factors this is checkpoint/resume. */
+did_status did_set_factors(did_ctx* ctx, const float* B, const float* C);
+
+/* Copy the stored residual out as float32 M x N column-major (host or device). */
+did_status did_get_residual(did_ctx* ctx, float* R);
+
+/* Copy the objective trace: obj[0] = f at the start point, obj[t] = f after
+ * sweep t.  At most cap values are written; *n receives the full length. */
+did_status did_get_trace(did_ctx* ctx, double* obj, int32_t cap, int32_t* n);
+
+did_status did_get_info(did_ctx* ctx, did_info* info);
+
+/* Message of the last failed call on this context ("" if none). */
+const char* did_last_error(const did_ctx* ctx);
+const char* did_status_string(did_status s);
+
+/* Free everything the context owns.  NULL is accepted. */
+void did_destroy(did_ctx* ctx);
+
+/* ------------------------------------------------------------------------
+ * Device-side input generators (synthetic workloads; the same counter-based
+ * generator as the host-side Python module `synth`).  Outputs are device
+ * buffers owned by the caller, M x N column-major with leading dimension M.
+ * ---------------------------------------------------------------------- */
+
+/* X = B0 C0 (+ sigma |N(0,1)|) with B0 ~ U[0,1) (M x K, stream 0) and C0 ~
+ * U[0,1) (coords = 0) or Exp(1) with a Bernoulli(zero_frac) share zeroed
+ * (coords = 1) (K x N, stream 1); then a Bernoulli(salt_frac) share of the
+ * entries is replaced by salt_value.  The product is accumulated in float32. */
+did_status did_generate_planted(float* X_dev, int64_t M, int64_t N, int32_t K, uint64_t seed,
+                                int32_t coords, double zero_frac, double sigma,
+                                double salt_frac, double salt_value, void* stream);
+
+/* Image-like X in [0,1]: a Bernoulli(zero_frac) share exact zeros, the rest Beta(2,2). */
+did_status did_generate_image(float* X_dev, int64_t M, int64_t N, uint64_t seed,
+                              double zero_frac, void* stream);
+
+/* Uniform[0,1) words of (seed, stream): out[i] = u(word i), i < n. */
+did_status did_generate_uniform(float* out_dev, int64_t n, uint64_t seed, int32_t stream_id,
+                                void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DID_H */

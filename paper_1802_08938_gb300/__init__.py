@@ -1,0 +1,304 @@
+"""Python binding of the GB300 DID library (libdid.so, C ABI in include/did.h).
+
+Argument marshalling only: every step of the factorisation runs in the CUDA
+library.  Functions keep the C names (``did_create``, ``did_sweep`` ...);
+``Context`` wraps a handle for convenience.  Arrays may be torch tensors (on
+the GPU or pinned/pageable host memory) or NumPy arrays; their storage is
+passed by pointer and must use the C ABI layouts:
+
+* X: M x N column-major == a C-contiguous (N, M) array, or an F-contiguous (M, N) one
+* B: M x K column-major == C-contiguous (K, M), or F-contiguous (M, K)
+* C: K x N row-major    == C-contiguous (K, N)
+
+There is no CPU fallback: importing this package without the built library
+raises ImportError (build it with ``__graft_entry__.build()`` or
+``python paper_1802_08938_gb300/_build.py``).
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdid.so")
+
+DID_OK, DID_PENDING, DID_EINVAL, DID_ENOMEM, DID_ECUDA, DID_ETIMEOUT, DID_E_TOO_LARGE, DID_EBUSY = (
+    0, 1, -1, -2, -3, -4, -5, -6)
+DID_FP32, DID_BF16R = 0, 1
+DID_ORDER_INTERLEAVED, DID_ORDER_DID = 0, 1
+DID_STOP_RELCHANGE, DID_STOP_PAPER_EPS = 0, 1
+
+
+class did_options(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int32),
+        ("order", ctypes.c_int32),
+        ("refresh_every", ctypes.c_int32),
+        ("stop", ctypes.c_int32),
+        ("init_scale", ctypes.c_int32),
+        ("grid_ctas", ctypes.c_int32),
+        ("B_init", ctypes.c_void_p),
+        ("C_init", ctypes.c_void_p),
+        ("stream", ctypes.c_void_p),
+        ("timeout_ns", ctypes.c_uint64),
+        ("debug_barrier_extra", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+
+class did_info(ctypes.Structure):
+    _fields_ = [
+        ("M", ctypes.c_int64), ("N", ctypes.c_int64), ("K", ctypes.c_int32),
+        ("precision", ctypes.c_int32), ("order", ctypes.c_int32),
+        ("grid_ctas", ctypes.c_int32), ("group_threads", ctypes.c_int32),
+        ("vecs_per_thread", ctypes.c_int32), ("ld", ctypes.c_int64),
+        ("sweeps_done", ctypes.c_int64), ("degenerate_events", ctypes.c_int64),
+        ("refreshes", ctypes.c_int64), ("device_bytes", ctypes.c_size_t),
+        ("sweep_launches", ctypes.c_int64), ("prologue_launches", ctypes.c_int64),
+        ("sweep_kernel_ms", ctypes.c_double), ("dense_launches", ctypes.c_int64),
+        ("dense_kernel_ms", ctypes.c_double),
+    ]
+
+
+class DIDError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (status_string(status), msg))
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libdid.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I64, I32, U64, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_double
+    CTX = ctypes.c_void_p
+    sig = {
+        "did_default_options": (None, [ctypes.POINTER(did_options)]),
+        "did_create": (I32, [P, I64, I64, I32, U64, ctypes.POINTER(CTX)]),
+        "did_create_ex": (I32, [P, I64, I64, I32, U64, ctypes.POINTER(did_options), ctypes.POINTER(CTX)]),
+        "did_sweep": (I32, [CTX, I32]),
+        "did_factor": (I32, [CTX, I32, D, ctypes.POINTER(I32), ctypes.POINTER(D)]),
+        "did_objective": (I32, [CTX, ctypes.POINTER(D)]),
+        "did_residual_objective": (I32, [CTX, ctypes.POINTER(D)]),
+        "did_refresh_residual": (I32, [CTX]),
+        "did_get_factors": (I32, [CTX, P, P]),
+        "did_set_factors": (I32, [CTX, P, P]),
+        "did_get_residual": (I32, [CTX, P]),
+        "did_get_trace": (I32, [CTX, ctypes.POINTER(D), I32, ctypes.POINTER(I32)]),
+        "did_get_info": (I32, [CTX, ctypes.POINTER(did_info)]),
+        "did_last_error": (ctypes.c_char_p, [CTX]),
+        "did_status_string": (ctypes.c_char_p, [I32]),
+        "did_destroy": (None, [CTX]),
+        "did_generate_planted": (I32, [P, I64, I64, I32, U64, I32, D, D, D, D, P]),
+        "did_generate_image": (I32, [P, I64, I64, U64, D, P]),
+        "did_generate_uniform": (I32, [P, I64, U64, I32, P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def status_string(s):
+    return _lib.did_status_string(int(s)).decode()
+
+
+def _ptr(a):
+    """Address of a tensor's / array's first element (None passes NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    if isinstance(a, int):
+        return a
+    raise TypeError("expected a torch tensor, NumPy array or address, got %r" % type(a))
+
+
+def _stream_of(stream):
+    if stream is not None:
+        return stream if isinstance(stream, int) else stream.cuda_stream
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return None
+
+
+def _check(status, ctx=None):
+    if status != DID_OK:
+        msg = _lib.did_last_error(ctx).decode() if ctx else ""
+        raise DIDError(status, msg)
+
+
+def default_options():
+    o = did_options()
+    _lib.did_default_options(ctypes.byref(o))
+    return o
+
+
+# ------------------------------------------------------------ C-named calls
+def did_create(X, M, N, K, seed, options=None):
+    h = ctypes.c_void_p()
+    if options is None:
+        st = _lib.did_create(_ptr(X), M, N, K, seed, ctypes.byref(h))
+    else:
+        st = _lib.did_create_ex(_ptr(X), M, N, K, seed, ctypes.byref(options), ctypes.byref(h))
+    _check(st)
+    return h
+
+
+did_create_ex = did_create
+
+
+def did_sweep(h, n):
+    _check(_lib.did_sweep(h, n), h)
+
+
+def did_factor(h, max_iter, tol):
+    it = ctypes.c_int32()
+    f = ctypes.c_double()
+    _check(_lib.did_factor(h, max_iter, tol, ctypes.byref(it), ctypes.byref(f)), h)
+    return it.value, f.value
+
+
+def did_objective(h):
+    f = ctypes.c_double()
+    _check(_lib.did_objective(h, ctypes.byref(f)), h)
+    return f.value
+
+
+def did_residual_objective(h):
+    f = ctypes.c_double()
+    _check(_lib.did_residual_objective(h, ctypes.byref(f)), h)
+    return f.value
+
+
+def did_refresh_residual(h):
+    _check(_lib.did_refresh_residual(h), h)
+
+
+def did_get_factors(h, B, C):
+    _check(_lib.did_get_factors(h, _ptr(B), _ptr(C)), h)
+
+
+def did_set_factors(h, B, C):
+    _check(_lib.did_set_factors(h, _ptr(B), _ptr(C)), h)
+
+
+def did_get_residual(h, R):
+    _check(_lib.did_get_residual(h, _ptr(R)), h)
+
+
+def did_get_trace(h):
+    n = ctypes.c_int32()
+    _check(_lib.did_get_trace(h, None, 0, ctypes.byref(n)), h)
+    buf = (ctypes.c_double * max(1, n.value))()
+    _check(_lib.did_get_trace(h, buf, n.value, ctypes.byref(n)), h)
+    return np.array(buf[: n.value], dtype=np.float64)
+
+
+def did_get_info(h):
+    i = did_info()
+    _check(_lib.did_get_info(h, ctypes.byref(i)), h)
+    return {k: getattr(i, k) for k, _ in did_info._fields_}
+
+
+def did_destroy(h):
+    _lib.did_destroy(h)
+
+
+def did_generate_planted(X_dev, M, N, K, seed, coords=0, zero_frac=0.0, sigma=0.0, salt_frac=0.0,
+                         salt_value=5.0, stream=None):
+    _check(_lib.did_generate_planted(_ptr(X_dev), M, N, K, seed, coords, zero_frac, sigma, salt_frac,
+                                     salt_value, _stream_of(stream)))
+
+
+def did_generate_image(X_dev, M, N, seed, zero_frac=0.8, stream=None):
+    _check(_lib.did_generate_image(_ptr(X_dev), M, N, seed, zero_frac, _stream_of(stream)))
+
+
+def did_generate_uniform(out_dev, n, seed, stream_id, stream=None):
+    _check(_lib.did_generate_uniform(_ptr(out_dev), n, seed, stream_id, _stream_of(stream)))
+
+
+# --------------------------------------------------------------- convenience
+class Context:
+    """Owns one did_ctx.  X is M x N column-major (C-contiguous (N, M))."""
+
+    def __init__(self, X, M, N, K, seed=0, precision=DID_FP32, order=DID_ORDER_INTERLEAVED,
+                 refresh_every=0, stop=DID_STOP_RELCHANGE, init_scale=False, grid_ctas=0,
+                 B_init=None, C_init=None, stream=None, timeout_ns=0, debug_barrier_extra=0):
+        o = default_options()
+        o.precision, o.order, o.refresh_every, o.stop = precision, order, refresh_every, stop
+        o.init_scale, o.grid_ctas = int(bool(init_scale)), grid_ctas
+        o.B_init, o.C_init = _ptr(B_init), _ptr(C_init)
+        o.stream = _stream_of(stream)
+        o.timeout_ns, o.debug_barrier_extra = timeout_ns, debug_barrier_extra
+        self.M, self.N, self.K = int(M), int(N), int(K)
+        self._keep = (X, B_init, C_init)
+        self.h = did_create(X, self.M, self.N, self.K, seed, o)
+        self._keep = None
+
+    def sweep(self, n=1):
+        did_sweep(self.h, n)
+
+    def factor(self, max_iter, tol):
+        return did_factor(self.h, max_iter, tol)
+
+    def objective(self):
+        return did_objective(self.h)
+
+    def residual_objective(self):
+        return did_residual_objective(self.h)
+
+    def refresh_residual(self):
+        did_refresh_residual(self.h)
+
+    def factors(self):
+        """(B as (M, K) float32, C as (K, N) float32) NumPy arrays on the host."""
+        Bt = np.empty((self.K, self.M), dtype=np.float32)    # column-major M x K
+        C = np.empty((self.K, self.N), dtype=np.float32)
+        did_get_factors(self.h, Bt, C)
+        return Bt.T, C
+
+    def set_factors(self, B, C):
+        Bt = np.ascontiguousarray(np.asarray(B, np.float32).T)
+        C = np.ascontiguousarray(np.asarray(C, np.float32))
+        did_set_factors(self.h, Bt, C)
+
+    def residual(self):
+        Rt = np.empty((self.N, self.M), dtype=np.float32)
+        did_get_residual(self.h, Rt)
+        return Rt.T
+
+    def trace(self):
+        return did_get_trace(self.h)
+
+    def info(self):
+        return did_get_info(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            did_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

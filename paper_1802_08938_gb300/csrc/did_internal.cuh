@@ -1,0 +1,251 @@
+// Internal declarations shared by the CUDA translation units of the DID
+// library: device helpers (bounded grid barrier, cache-hinted vector loads,
+// bfloat16 packing, the counter-based generator) and the host-side launcher
+// interfaces that the C ABI in did_api.cu calls.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/did.h"
+
+namespace did {
+
+// ----------------------------------------------------------------- constants
+constexpr int kSweepThreads = 512;    // threads of one sweep CTA
+constexpr int kMaxGroups = 15;        // named barriers 1..15 (0 is __syncthreads)
+constexpr int kWarps = kSweepThreads / 32;
+
+// Device error word values (ctrl[1]).
+constexpr int kDevErrTimeout = 1;     // a grid wait ran out of time
+
+// Layout of the per-context control words (zeroed before every sweep launch).
+struct Ctrl {
+  unsigned bar;        // grid-barrier arrival counter
+  int err;             // device error word
+  int stopped;         // 1 when the stopping rule held inside the launch
+  int sweeps;          // sweeps completed by the launch
+};
+
+// ------------------------------------------------------------ device helpers
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ int ld_volatile(const int* p) { return *(const volatile int*)p; }
+
+// Grid-wide barrier for a co-resident (cooperative) grid.  Every CTA adds one
+// arrival to a monotone counter and waits until it reaches `target`.  The wait
+// is bounded twice: by `timeout_ns` of %globaltimer and by an iteration cap.
+// On expiry the error word is set and false is returned; a CTA that sees the
+// error word set by another CTA also returns false.  No wait is unbounded.
+__device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned target, int* err,
+                                          uint64_t timeout_ns) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();
+    atomicAdd(bar, 1u);
+    const uint64_t t0 = globaltimer_ns();
+    unsigned iters = 0;
+    while ((int)(ld_acquire_gpu(bar) - target) < 0) {
+      if (ld_volatile(err) != 0) { ok = 0; break; }
+      if (++iters > (1u << 28) || globaltimer_ns() - t0 > timeout_ns) {
+        atomicCAS(err, 0, kDevErrTimeout);
+        ok = 0;
+        break;
+      }
+      __nanosleep(40);
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Named barrier over `nthreads` threads (a multiple of 32) with id 1..15.
+__device__ __forceinline__ void named_bar(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+__device__ __forceinline__ double warp_sum_f64(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ float warp_sum_f32(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Deterministic block-wide float64 sum (fixed tree, fixed warp order).  All
+// threads must call it; the result is valid in every thread.  `scratch` holds
+// kWarps doubles of shared memory.
+__device__ __forceinline__ double block_sum_f64(double v, double* scratch) {
+  v = warp_sum_f64(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) scratch[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  const int nw = blockDim.x >> 5;
+  for (int i = 0; i < nw; ++i) s += scratch[i];
+  return s;
+}
+
+// Sum of n doubles in global memory (written by other CTAs) in a fixed order:
+// lane l takes indices l, l+32, ... then a fixed xor tree.  Warp-collective.
+__device__ __forceinline__ double warp_sum_global_f64(const double* p, int n, int stride) {
+  const int l = threadIdx.x & 31;
+  double s = 0.0;
+  for (int i = l; i < n; i += 32) s += __ldcg(p + (size_t)i * stride);
+  return warp_sum_f64(s);
+}
+
+// ----------------------------------------------------------- 16-byte vectors
+// FP32 residual: 4 rows per vector.  BF16 residual: 8 rows per vector.
+template <bool BF16> struct Vec;
+
+template <> struct Vec<false> {
+  static constexpr int kRows = 4;
+  typedef float4 raw;
+  __device__ __forceinline__ static void unpack(const raw& v, float* f) {
+    f[0] = v.x; f[1] = v.y; f[2] = v.z; f[3] = v.w;
+  }
+  __device__ __forceinline__ static raw pack(const float* f) {
+    return make_float4(f[0], f[1], f[2], f[3]);
+  }
+};
+
+template <> struct Vec<true> {
+  static constexpr int kRows = 8;
+  typedef uint4 raw;
+  __device__ __forceinline__ static void unpack(const raw& v, float* f) {
+    const unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      // bfloat16 -> float32 is exact: the 16 bits become the high half.
+      f[2 * i] = __uint_as_float(w[i] << 16);
+      f[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+    }
+  }
+  __device__ __forceinline__ static raw pack(const float* f) {
+    unsigned w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      __nv_bfloat162 h = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);  // round to nearest even
+      w[i] = *reinterpret_cast<unsigned*>(&h);
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
+  }
+};
+
+// --------------------------------------------------- counter-based generator
+// SplitMix64 output function (Steele, Lea and Flood 2014) and the stream
+// definition: key = mix64(seed + (stream+1) G), word i = mix64(key + (i+1) G).
+constexpr uint64_t kGolden = 0x9E3779B97F4A7C15ull;
+
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__host__ __device__ __forceinline__ uint64_t stream_key(uint64_t seed, int stream) {
+  return mix64(seed + (uint64_t)(stream + 1) * kGolden);
+}
+__host__ __device__ __forceinline__ uint64_t stream_word(uint64_t key, uint64_t i) {
+  return mix64(key + (i + 1) * kGolden);
+}
+__host__ __device__ __forceinline__ float u01_f32(uint64_t w) {
+  return (float)(uint32_t)(w >> 40) * 5.9604644775390625e-8f;  // 2^-24
+}
+__host__ __device__ __forceinline__ double u01_f64(uint64_t w) {
+  return (double)(w >> 11) * 1.1102230246251565e-16;              // 2^-53
+}
+
+// ------------------------------------------------------------ host launchers
+struct SweepArgs {
+  void* R;            // ld x N residual (float or bf16)
+  float* B;           // ld x K, column-major, rows >= M are zero
+  float* C;           // K x N, row-major
+  float* P;           // [grid][ld] per-CTA partials of R c^T
+  double* CCp;        // [grid] per-CTA partials of ||c||^2
+  double* Sp;         // [grid][2] per-CTA partials of ||b'||^2 and b'.b
+  double* OBJp;       // [grid] per-CTA partials of sum R^2
+  float* bold;        // [ld] previous b_k while c_k is updated
+  Ctrl* ctrl;         // barrier, error word, stop flag, sweep count
+  double* trace;      // trace[s] = objective after sweep s of this launch
+  unsigned long long* degen;  // count of blocks left unchanged (zero norm)
+  int64_t N;
+  int M, ld, K;
+  int GS, NG;         // threads per column group, groups per CTA
+  int n_sweeps;       // sweeps of this launch
+  int prologue;       // 1: first form the partials of R c_1^T from R
+  double f_prev;      // objective before the first sweep of this launch
+  double f0;          // objective at the start point (paper eps rule)
+  int stop_rule;      // 0 none, 1 relative change, 2 paper eps
+  double tol;
+  int order;          // did_order
+  int bar_extra;      // test hook: extra arrivals each grid wait expects
+  uint64_t timeout_ns;
+};
+
+struct SweepPlan {
+  int grid, GS, NG, NR;
+  size_t smem;
+  const void* func;
+};
+
+// Choose the column-group shape and grid for (ld, precision); fills *plan.
+did_status plan_sweep(int ld, bool bf16, int grid_override, SweepPlan* plan, char* err, size_t errlen);
+cudaError_t launch_sweep(const SweepPlan& plan, const SweepArgs& args, cudaStream_t s);
+
+// Dense pass over tiles of X - B C:
+//   mode 0: R = X - B C stored (float or bf16); sums[0] += sum R^2
+//   mode 1: no store; sums[0] += sum (X - BC)^2
+//   mode 2: no store; sums[1] += sum X (BC), sums[2] += sum (BC)^2
+// Partial sums land in part[grid][3]; the host adds them in index order.
+struct DenseArgs {
+  const float* X; void* R; const float* B; const float* C;
+  double* part;
+  int M, ld, K;
+  int64_t N;
+  int mode;
+  int bf16;
+};
+int dense_grid();
+cudaError_t launch_dense(const DenseArgs& a, cudaStream_t s);
+
+// Generators.
+cudaError_t launch_gen_uniform_padded(float* out, int rows, int ld, int cols, uint64_t seed,
+                                      int stream_id, cudaStream_t s);  // out[c*ld + r] = word c*rows + r
+cudaError_t launch_gen_uniform(float* out, int64_t n, uint64_t seed, int stream_id, cudaStream_t s);
+cudaError_t launch_gen_exp_coords(float* out, int64_t K, int64_t N, uint64_t seed, double zero_frac,
+                                  cudaStream_t s);
+cudaError_t launch_gen_planted_x(float* X, const float* B0, const float* C0, int M, int64_t N, int K,
+                                 uint64_t seed, double sigma, double salt_frac, double salt_value,
+                                 cudaStream_t s);
+cudaError_t launch_gen_image(float* X, int M, int64_t N, uint64_t seed, double zero_frac, cudaStream_t s);
+
+// Elementwise helpers.
+cudaError_t launch_check_nonneg_finite(const float* X, int rows, int ld, int64_t cols,
+                                       unsigned long long* bad, cudaStream_t s);
+cudaError_t launch_scale(float* p, int64_t n, float s, cudaStream_t st);
+cudaError_t launch_bf16_to_f32(const void* R, float* out, int rows, int ld_in, int ld_out,
+                               int64_t cols, cudaStream_t s);
+
+}  // namespace did
