@@ -386,14 +386,25 @@ did_status plan_sweep(int ld, bool bf16, int grid_override, SweepPlan* plan, cha
     snprintf(err, errlen, "sweep shared memory %zu bytes exceeds the per-CTA limit", plan->smem);
     return DID_E_TOO_LARGE;
   }
-  cudaError_t e = cudaFuncSetAttribute(plan->func, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)plan->smem);
+  // The cap is a property of the kernel function shared by every context: set
+  // it to the device maximum (not to this plan's size), so that plans with
+  // different ld on the same kernel variant can all launch.
+  int dev = 0, sms = 0, per_sm = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa{};
+  cudaError_t e = cudaFuncGetAttributes(&fa, plan->func);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(plan->func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)fa.sharedSizeBytes);
   if (e != cudaSuccess) {
     snprintf(err, errlen, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
     return DID_ECUDA;
   }
-  int dev = 0, sms = 0, per_sm = 0;
-  cudaGetDevice(&dev);
+  if (plan->smem + fa.sharedSizeBytes > (size_t)optin) {
+    snprintf(err, errlen, "sweep shared memory %zu bytes exceeds the per-CTA limit", plan->smem);
+    return DID_E_TOO_LARGE;
+  }
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan->func, kSweepThreads, plan->smem);
   if (e != cudaSuccess || per_sm < 1) {
@@ -412,3 +423,4 @@ cudaError_t launch_sweep(const SweepPlan& plan, const SweepArgs& args, cudaStrea
 }
 
 }  // namespace did
+

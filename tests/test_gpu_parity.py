@@ -217,6 +217,28 @@ def test_barrier_timeout_is_reported_and_context_survives(did):
         assert len(ok.trace()) == 3
 
 
+def test_contexts_of_different_sizes_interleave(did):
+    """Two live contexts whose plans share a kernel variant but differ in shared
+    memory (M = 200 and M = 216, ld 208 and 224) sweep alternately."""
+    out = []
+    for M in (200, 216):
+        X, _, _ = W.planted(M, 500, 6, seed=M, sigma=0.01)
+        out.append((X, did.Context(np.ascontiguousarray(X.T), M, 500, 6, seed=M)))
+    try:
+        for _ in range(2):
+            for X, ctx in out:
+                ctx.sweep(2)
+        for X, ctx in out:
+            M = X.shape[0]
+            B0, C0 = W.init_factors(M, 500, 6, M)
+            ref = O.factor(X, B0, C0, order="hals", max_iter=4, stop="none")
+            B, C = ctx.factors()
+            assert rel_fro(B, ref["B"]) <= TOL_FACTOR and rel_fro(C, ref["C"]) <= TOL_FACTOR
+    finally:
+        for _, ctx in out:
+            ctx.close()
+
+
 def test_device_pointer_inputs(did):
     import torch
     X, M, N, K = W.make("planted_uniform_200x1000_k10", seed=9, M=120, N=333, K=6)
