@@ -132,6 +132,28 @@ did_status did_sweep(did_ctx* ctx, int32_t n_sweeps);
 did_status did_factor(did_ctx* ctx, int32_t max_iter, double tol, int32_t* iters_done,
                       double* final_obj);
 
+/* Sweep without any device allocation, for callers that cannot call
+ * cudaMalloc where they run: code inside another runtime's allocator or
+ * memory-planning hooks, or a host that fixed its device memory budget up
+ * front.  The paper has no counterpart; this is a library convenience.
+ * It runs n_sweeps sweeps of the same kernel as did_sweep (interleaved order,
+ * float32 residual) on caller-owned device buffers, updated in place:
+ *   R : ld x N column-major residual X - B C, ld a multiple of 4, ld >= M,
+ *       rows M..ld-1 zero, 16-byte aligned;
+ *   B : ld x K column-major, rows M..ld-1 zero, 16-byte aligned;
+ *   C : K x N row-major.
+ * trace (may be NULL; host or device) receives 1/2 ||R||^2 after each sweep.
+ * Its scratch (grid partials, per-CTA scalars, control words) is one static
+ * device array of 6 MiB that every GPU which loads the library holds until
+ * the process exits; limits: ld <= 8192, n_sweeps <= 1024, at most 160 CTAs
+ * (DID_E_TOO_LARGE beyond them).  It calls no cudaMalloc/cudaFree.  The first
+ * call on a device looks up that device's address of the array, so make it
+ * before any stream capture.  All calls share the array: calls that overlap
+ * on the GPU (other streams, other threads) race and must be serialised by
+ * the caller.  Synchronises `stream` (NULL = legacy default stream). */
+did_status did_sweep_static(float* R, int64_t ld, float* B, float* C, int64_t M, int64_t N, int32_t K,
+                            int32_t n_sweeps, double* trace, void* stream);
+
 /* Exact objective 1/2 ||X - B C||_F^2 from X, B, C in a fresh pass
  * (float32 products, float64 accumulation); R is not touched. */
 did_status did_objective(did_ctx* ctx, double* obj);

@@ -78,6 +78,7 @@ def _load():
         "did_create": (I32, [P, I64, I64, I32, U64, ctypes.POINTER(CTX)]),
         "did_create_ex": (I32, [P, I64, I64, I32, U64, ctypes.POINTER(did_options), ctypes.POINTER(CTX)]),
         "did_sweep": (I32, [CTX, I32]),
+        "did_sweep_static": (I32, [P, I64, P, P, I64, I64, I32, I32, P, P]),
         "did_factor": (I32, [CTX, I32, D, ctypes.POINTER(I32), ctypes.POINTER(D)]),
         "did_objective": (I32, [CTX, ctypes.POINTER(D)]),
         "did_residual_objective": (I32, [CTX, ctypes.POINTER(D)]),
@@ -161,6 +162,12 @@ did_create_ex = did_create
 
 def did_sweep(h, n):
     _check(_lib.did_sweep(h, n), h)
+
+
+def did_sweep_static(R, ld, B, C, M, N, K, n_sweeps, trace=None, stream=None):
+    """Sweeps on caller-owned device buffers with no device allocation."""
+    _check(_lib.did_sweep_static(_ptr(R), ld, _ptr(B), _ptr(C), M, N, K, n_sweeps, _ptr(trace),
+                                 _stream_of(stream)))
 
 
 def did_factor(h, max_iter, tol):

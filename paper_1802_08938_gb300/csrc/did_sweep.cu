@@ -27,6 +27,7 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <mutex>
 
 namespace did {
 
@@ -424,3 +425,131 @@ cudaError_t launch_sweep(const SweepPlan& plan, const SweepArgs& args, cudaStrea
 
 }  // namespace did
 
+// ---------------------------------------------------------------------------
+// did_sweep_static: the same sweep kernel for callers that cannot allocate
+// device memory (no cudaMalloc is allowed where they run, e.g. inside another
+// runtime's allocator hooks or under a fixed memory plan).  Its scratch --
+// the grid partials of R c_k^T, the per-CTA scalars, the control words and
+// the trace window -- lives in one file-scope device array that every GPU
+// which loads this library holds until the process exits.
+// ---------------------------------------------------------------------------
+namespace did {
+namespace {
+
+constexpr size_t kStaticScratchBytes = (size_t)6 << 20;   // 6 MiB per device
+constexpr int kStaticMaxLd = 8192;                          // rows (ld) limit
+constexpr int kStaticMaxGrid = 160;                         // CTAs limit
+constexpr int kStaticMaxSweeps = 1024;                      // sweeps per call
+constexpr int kStaticMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+// Device addresses of g_static_scratch, one per device, set up on first use.
+void* g_static_ptr[kStaticMaxDevices];
+std::mutex g_static_mu;
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct StaticLayout {
+  size_t ctrl, degen, trace, ccp, sp, objp, bold, p, end;
+};
+
+StaticLayout static_layout() {
+  StaticLayout L;
+  size_t o = 0;
+  L.ctrl = o;  o = align256(o + sizeof(Ctrl));
+  L.degen = o; o = align256(o + sizeof(unsigned long long));
+  L.trace = o; o = align256(o + sizeof(double) * kStaticMaxSweeps);
+  L.ccp = o;   o = align256(o + sizeof(double) * kStaticMaxGrid);
+  L.sp = o;    o = align256(o + sizeof(double) * 2 * kStaticMaxGrid);
+  L.objp = o;  o = align256(o + sizeof(double) * kStaticMaxGrid);
+  L.bold = o;  o = align256(o + sizeof(float) * kStaticMaxLd);
+  L.p = o;     o = align256(o + sizeof(float) * (size_t)kStaticMaxGrid * kStaticMaxLd);
+  L.end = o;
+  return L;
+}
+static_assert(sizeof(Ctrl) <= 256, "control words fit their slot");
+
+// Device address of the scratch array for the current device (set-up once
+// per device, with that device current).
+did_status static_scratch(unsigned char** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices) return DID_ECUDA;
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return DID_ECUDA;
+    }
+    g_static_ptr[dev] = p;
+  }
+  *out = static_cast<unsigned char*>(g_static_ptr[dev]);
+  return DID_OK;
+}
+
+}  // namespace
+
+}  // namespace did
+
+extern "C" did_status did_sweep_static(float* R, int64_t ld, float* B, float* C, int64_t M, int64_t N, int32_t K,
+                                       int32_t n_sweeps, double* trace, void* stream) {
+  using namespace did;
+  if (!R || !B || !C || M < 1 || N < 1 || K < 1 || K > M || K > N || ld < M || ld % 4 != 0 ||
+      n_sweeps < 0 || ((uintptr_t)R & 15) || ((uintptr_t)B & 15))
+    return DID_EINVAL;
+  if (ld > kStaticMaxLd || n_sweeps > kStaticMaxSweeps) return DID_E_TOO_LARGE;
+  static_assert(sizeof(g_static_scratch) >= (size_t)5 << 20, "scratch holds the grid partials");
+  const StaticLayout L = static_layout();
+  if (L.end > kStaticScratchBytes) return DID_E_TOO_LARGE;
+  unsigned char* base = nullptr;
+  did_status st = static_scratch(&base);
+  if (st != DID_OK) return st;
+  SweepPlan plan{};
+  char err[256];
+  st = plan_sweep((int)ld, false, kStaticMaxGrid, &plan, err, sizeof(err));
+  if (st != DID_OK) return st;
+  if (plan.grid > kStaticMaxGrid) return DID_E_TOO_LARGE;
+  cudaStream_t s = (cudaStream_t)stream;
+
+  SweepArgs a{};
+  a.R = R;
+  a.B = B;
+  a.C = C;
+  a.P = reinterpret_cast<float*>(base + L.p);
+  a.CCp = reinterpret_cast<double*>(base + L.ccp);
+  a.Sp = reinterpret_cast<double*>(base + L.sp);
+  a.OBJp = reinterpret_cast<double*>(base + L.objp);
+  a.bold = reinterpret_cast<float*>(base + L.bold);
+  a.ctrl = reinterpret_cast<Ctrl*>(base + L.ctrl);
+  a.trace = reinterpret_cast<double*>(base + L.trace);
+  a.degen = reinterpret_cast<unsigned long long*>(base + L.degen);
+  a.N = N;
+  a.M = (int)M;
+  a.ld = (int)ld;
+  a.K = K;
+  a.GS = plan.GS;
+  a.NG = plan.NG;
+  a.n_sweeps = n_sweeps;
+  a.prologue = 1;       // the partials of R c_1^T are always re-formed from R
+  a.stop_rule = 0;
+  a.timeout_ns = 4000000000ull;
+  // The array keeps the previous call's contents: clear the control words and
+  // the event counter, which must start at zero.
+  if (cudaMemsetAsync(base + L.ctrl, 0, sizeof(Ctrl), s) != cudaSuccess ||
+      cudaMemsetAsync(base + L.degen, 0, sizeof(unsigned long long), s) != cudaSuccess ||
+      launch_sweep(plan, a, s) != cudaSuccess) {
+    cudaGetLastError();
+    return DID_ECUDA;
+  }
+  Ctrl h{};
+  if (cudaMemcpyAsync(&h, base + L.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      (trace && n_sweeps > 0 &&
+       cudaMemcpyAsync(trace, base + L.trace, sizeof(double) * n_sweeps, cudaMemcpyDefault, s) != cudaSuccess) ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return DID_ECUDA;
+  }
+  if (h.err != 0) return DID_ETIMEOUT;
+  return DID_OK;
+}
