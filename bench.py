@@ -213,6 +213,10 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16r"])
+    ap.add_argument("--shape", default=None,
+                    help="M,N,K override of the workload's sizes (same generator); for profiling small cases")
+    ap.add_argument("--phases", action="store_true",
+                    help="also report the per-k phase split of the last timed sweep (globaltimer stamps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -234,7 +238,9 @@ def main():
     __graft_entry__.build()
     import paper_1802_08938_gb300 as did
 
-    w = WORKLOADS[args.workload]
+    w = dict(WORKLOADS[args.workload])
+    if args.shape:
+        w["M"], w["N"], w["K"] = (int(v) for v in args.shape.split(","))
     M, N, K = w["M"], w["N"], w["K"]
     prec = did.DID_BF16R if args.precision == "bf16r" else did.DID_FP32
     s_bytes = 2 if prec == did.DID_BF16R else 4
@@ -254,7 +260,8 @@ def main():
             torch.distributed.barrier()
 
     ctx = did.Context(X, M, N, K, seed=seed, precision=prec, refresh_every=w["refresh_every"],
-                      init_scale=w["init_scale"], stream=stream)
+                      init_scale=w["init_scale"], stream=stream,
+                      flags=did.DID_FLAG_PHASE_TIMES if args.phases else 0)
     for _ in range(args.warmup):
         ctx.sweep(1)
     info0 = ctx.info()
@@ -265,13 +272,27 @@ def main():
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
+    step_ms = []
+    last = info0["sweep_kernel_ms"] + info0["dense_kernel_ms"]
     for _ in range(args.steps):
         ctx.sweep(1)
+        cur = ctx.info()
+        now = cur["sweep_kernel_ms"] + cur["dense_kernel_ms"]
+        step_ms.append(round(now - last, 3))
+        last = now
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
     info1 = ctx.info()
+    phases = None
+    if args.phases:
+        t = ctx.phase_times().astype("int64")
+        if len(t):
+            d = lambda a, b: float(((t[:, b] - t[:, a]) / 1e3).mean())
+            phases = {"us_per_k": {"b_reduce+wait1": d(0, 1), "c_pass": d(1, 2), "wait2": d(2, 3),
+                                   "gap_to_next_k": float((t[1:, 0] - t[:-1, 3]).mean() / 1e3) if len(t) > 1 else 0.0},
+                      "k_steps": int(len(t))}
     ms = ev0.elapsed_time(ev1)
     if ws > 1:
         t = torch.tensor([ms], device="cuda")
@@ -322,7 +343,7 @@ def main():
         del X
 
     cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and not args.shape:
         cpu = cpu_baseline(args.workload)
 
     if rank == 0:
@@ -342,6 +363,8 @@ def main():
                          "kernel_ms_per_sweep": kms / max(1, args.steps)},
             "e2e": e2e,
             "gpu_launches": int(gpu_launches),
+            "step_kernel_ms": step_ms,
+            "phases": phases,
             "cpu_baseline": cpu,
             "clocks": clk,
         }

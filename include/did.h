@@ -77,8 +77,14 @@ typedef struct {
     void* stream;           /* cudaStream_t to order all work on; NULL = legacy default stream */
     uint64_t timeout_ns;    /* limit of every device-side grid wait; 0 = 4 s */
     int32_t debug_barrier_extra; /* test hook: arrivals a grid wait expects beyond the grid (0 in use) */
-    int32_t reserved;
+    int32_t flags;          /* DID_FLAG_* bits */
 } did_options;
+
+/* did_options.flags: record %globaltimer stamps of the sweep phases (CTA 0):
+ * per k, the start of the b-reduce, the end of the first grid wait, the end of
+ * the c-pass and the end of the second grid wait.  Read with
+ * did_get_phase_times; costs four 8-byte stores per k. */
+#define DID_FLAG_PHASE_TIMES 1
 
 typedef struct {
     int64_t M, N;
@@ -87,6 +93,8 @@ typedef struct {
     int32_t grid_ctas;       /* persistent grid of the sweep kernel */
     int32_t group_threads;   /* threads cooperating on one column */
     int32_t vecs_per_thread; /* 16-byte vectors of a column each thread holds */
+    int32_t column_units;    /* units (contiguous column ranges) per pass */
+    int32_t dynamic_units;   /* 1: column groups take units from a counter */
     int64_t ld;              /* padded leading dimension of the device X and R */
     int64_t sweeps_done;
     int64_t degenerate_events; /* blocks left unchanged because a norm was exactly zero */
@@ -180,6 +188,12 @@ did_status did_get_residual(did_ctx* ctx, float* R);
 did_status did_get_trace(did_ctx* ctx, double* obj, int32_t cap, int32_t* n);
 
 did_status did_get_info(did_ctx* ctx, did_info* info);
+
+/* Phase stamps of the last sweep launch (DID_FLAG_PHASE_TIMES): stamps[4*i+p]
+ * in nanoseconds for step i = sweep*K + k and phase p (0 b-reduce start, 1
+ * after the first grid wait, 2 c-pass end, 3 after the second grid wait).
+ * At most cap values are written; *n receives the number recorded. */
+did_status did_get_phase_times(did_ctx* ctx, uint64_t* stamps, int32_t cap, int32_t* n);
 
 /* Message of the last failed call on this context ("" if none). */
 const char* did_last_error(const did_ctx* ctx);

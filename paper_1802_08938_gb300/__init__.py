@@ -28,6 +28,7 @@ DID_OK, DID_PENDING, DID_EINVAL, DID_ENOMEM, DID_ECUDA, DID_ETIMEOUT, DID_E_TOO_
 DID_FP32, DID_BF16R = 0, 1
 DID_ORDER_INTERLEAVED, DID_ORDER_DID = 0, 1
 DID_STOP_RELCHANGE, DID_STOP_PAPER_EPS = 0, 1
+DID_FLAG_PHASE_TIMES = 1
 
 
 class did_options(ctypes.Structure):
@@ -43,7 +44,7 @@ class did_options(ctypes.Structure):
         ("stream", ctypes.c_void_p),
         ("timeout_ns", ctypes.c_uint64),
         ("debug_barrier_extra", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("flags", ctypes.c_int32),
     ]
 
 
@@ -52,7 +53,8 @@ class did_info(ctypes.Structure):
         ("M", ctypes.c_int64), ("N", ctypes.c_int64), ("K", ctypes.c_int32),
         ("precision", ctypes.c_int32), ("order", ctypes.c_int32),
         ("grid_ctas", ctypes.c_int32), ("group_threads", ctypes.c_int32),
-        ("vecs_per_thread", ctypes.c_int32), ("ld", ctypes.c_int64),
+        ("vecs_per_thread", ctypes.c_int32), ("column_units", ctypes.c_int32),
+        ("dynamic_units", ctypes.c_int32), ("ld", ctypes.c_int64),
         ("sweeps_done", ctypes.c_int64), ("degenerate_events", ctypes.c_int64),
         ("refreshes", ctypes.c_int64), ("device_bytes", ctypes.c_size_t),
         ("sweep_launches", ctypes.c_int64), ("prologue_launches", ctypes.c_int64),
@@ -88,6 +90,7 @@ def _load():
         "did_get_residual": (I32, [CTX, P]),
         "did_get_trace": (I32, [CTX, ctypes.POINTER(D), I32, ctypes.POINTER(I32)]),
         "did_get_info": (I32, [CTX, ctypes.POINTER(did_info)]),
+        "did_get_phase_times": (I32, [CTX, ctypes.POINTER(ctypes.c_uint64), I32, ctypes.POINTER(I32)]),
         "did_last_error": (ctypes.c_char_p, [CTX]),
         "did_status_string": (ctypes.c_char_p, [I32]),
         "did_destroy": (None, [CTX]),
@@ -219,6 +222,15 @@ def did_get_info(h):
     return {k: getattr(i, k) for k, _ in did_info._fields_}
 
 
+def did_get_phase_times(h):
+    """Phase stamps of the last sweep launch as an (steps, 4) uint64 array (ns)."""
+    n = ctypes.c_int32()
+    _check(_lib.did_get_phase_times(h, None, 0, ctypes.byref(n)), h)
+    buf = (ctypes.c_uint64 * max(1, n.value))()
+    _check(_lib.did_get_phase_times(h, buf, n.value, ctypes.byref(n)), h)
+    return np.array(buf[: n.value], dtype=np.uint64).reshape(-1, 4)
+
+
 def did_destroy(h):
     _lib.did_destroy(h)
 
@@ -243,13 +255,13 @@ class Context:
 
     def __init__(self, X, M, N, K, seed=0, precision=DID_FP32, order=DID_ORDER_INTERLEAVED,
                  refresh_every=0, stop=DID_STOP_RELCHANGE, init_scale=False, grid_ctas=0,
-                 B_init=None, C_init=None, stream=None, timeout_ns=0, debug_barrier_extra=0):
+                 B_init=None, C_init=None, stream=None, timeout_ns=0, debug_barrier_extra=0, flags=0):
         o = default_options()
         o.precision, o.order, o.refresh_every, o.stop = precision, order, refresh_every, stop
         o.init_scale, o.grid_ctas = int(bool(init_scale)), grid_ctas
         o.B_init, o.C_init = _ptr(B_init), _ptr(C_init)
         o.stream = _stream_of(stream)
-        o.timeout_ns, o.debug_barrier_extra = timeout_ns, debug_barrier_extra
+        o.timeout_ns, o.debug_barrier_extra, o.flags = timeout_ns, debug_barrier_extra, flags
         self.M, self.N, self.K = int(M), int(N), int(K)
         self._keep = (X, B_init, C_init)
         self.h = did_create(X, self.M, self.N, self.K, seed, o)
@@ -292,6 +304,9 @@ class Context:
 
     def info(self):
         return did_get_info(self.h)
+
+    def phase_times(self):
+        return did_get_phase_times(self.h)
 
     def close(self):
         if getattr(self, "h", None):

@@ -41,6 +41,9 @@ struct did_ctx {
   unsigned long long* degen = nullptr;
   double* dense_part = nullptr;
   unsigned long long* bad = nullptr;
+  uint64_t* tstamp = nullptr;       // phase stamps (DID_FLAG_PHASE_TIMES)
+  int tstamp_cap = 0;
+  int tstamp_n = 0;
   Ctrl* ctrl_host = nullptr;        // pinned
   double* trace_host = nullptr;     // pinned, kMaxSweepsPerLaunch
   double* part_host = nullptr;      // pinned, 3 * dense grid
@@ -202,6 +205,11 @@ did_status launch_sweeps(did_ctx* c, int n, int stop_rule, double tol, int* done
   a.K = c->K;
   a.GS = c->plan.GS;
   a.NG = c->plan.NG;
+  a.D = c->plan.D;
+  a.units = c->plan.units;
+  a.nunits = c->plan.nunits;
+  a.dynamic = c->plan.dynamic;
+  a.npart = c->plan.npart;
   a.n_sweeps = n;
   a.prologue = c->need_prologue ? 1 : 0;
   a.f_prev = c->trace.back();
@@ -211,6 +219,9 @@ did_status launch_sweeps(did_ctx* c, int n, int stop_rule, double tol, int* done
   a.order = c->opt.order;
   a.bar_extra = c->opt.debug_barrier_extra;
   a.timeout_ns = c->opt.timeout_ns ? c->opt.timeout_ns : kDefaultTimeoutNs;
+  a.tstamp = c->tstamp;
+  a.tstamp_cap = c->tstamp_cap;
+  c->tstamp_n = c->tstamp ? (int)std::min<int64_t>((int64_t)n * c->K, c->tstamp_cap) : 0;
   DID_CUDA(c, cudaMemsetAsync(c->ctrl, 0, sizeof(Ctrl), c->stream));
   DID_CUDA(c, cudaEventRecord(c->ev0, c->stream));
   DID_CUDA(c, did::launch_sweep(c->plan, a, c->stream));
@@ -322,7 +333,7 @@ static did_status create_impl(did_ctx* c, const float* X, uint64_t seed) {
   const int64_t M = c->M, N = c->N;
   const int K = c->K;
   char err[256] = {0};
-  did_status st = did::plan_sweep(c->ld, c->bf16, c->opt.grid_ctas, &c->plan, err, sizeof(err));
+  did_status st = did::plan_sweep(c->ld, c->N, c->bf16, c->opt.grid_ctas, 0, &c->plan, err, sizeof(err));
   if (st != DID_OK) return fail(c, st, "%s", err);
   c->dense_grid = did::dense_grid();
   DID_CUDA(c, cudaEventCreate(&c->ev0));
@@ -340,16 +351,21 @@ static did_status create_impl(did_ctx* c, const float* X, uint64_t seed) {
   ALLOC(R, elems * (c->bf16 ? 2 : 4));
   ALLOC(B, (size_t)c->ld * K * sizeof(float));
   ALLOC(C, (size_t)K * N * sizeof(float));
-  ALLOC(P, (size_t)G * c->ld * sizeof(float));
-  ALLOC(CCp, (size_t)G * sizeof(double));
+  const size_t U = (size_t)std::max(c->plan.npart, G);
+  ALLOC(P, U * c->ld * sizeof(float));
+  ALLOC(CCp, U * sizeof(double));
   ALLOC(Sp, (size_t)2 * G * sizeof(double));
-  ALLOC(OBJp, (size_t)G * sizeof(double));
+  ALLOC(OBJp, U * sizeof(double));
   ALLOC(bold, (size_t)c->ld * sizeof(float));
   ALLOC(ctrl, sizeof(Ctrl));
   ALLOC(trace_dev, sizeof(double) * kMaxSweepsPerLaunch);
   ALLOC(degen, sizeof(unsigned long long));
   ALLOC(dense_part, sizeof(double) * 3 * c->dense_grid);
   ALLOC(bad, sizeof(unsigned long long));
+  if (c->opt.flags & DID_FLAG_PHASE_TIMES) {
+    c->tstamp_cap = 1 << 14;
+    ALLOC(tstamp, sizeof(uint64_t) * 4 * c->tstamp_cap);
+  }
 #undef ALLOC
   st = host_alloc(c, &p, sizeof(Ctrl));
   if (st != DID_OK) return st;
@@ -411,7 +427,7 @@ did_status did_create_ex(const float* X, int64_t M, int64_t N, int32_t K, uint64
   if (opt) o = *opt; else did_default_options(&o);
   if ((o.precision != DID_FP32 && o.precision != DID_BF16R) || (o.order != DID_ORDER_INTERLEAVED) ||
       (o.stop != DID_STOP_RELCHANGE && o.stop != DID_STOP_PAPER_EPS) || o.refresh_every < 0 ||
-      o.debug_barrier_extra < 0)
+      o.debug_barrier_extra < 0 || (o.flags & ~DID_FLAG_PHASE_TIMES))
     return DID_EINVAL;
   did_ctx* c = new did_ctx();
   c->M = M;
@@ -546,6 +562,8 @@ did_status did_get_info(did_ctx* c, did_info* info) {
   info->grid_ctas = c->plan.grid;
   info->group_threads = c->plan.GS;
   info->vecs_per_thread = c->plan.NR;
+  info->column_units = c->plan.nunits;
+  info->dynamic_units = c->plan.dynamic;
   info->ld = c->ld;
   info->sweeps_done = c->sweeps_done;
   unsigned long long d = 0;
@@ -561,6 +579,18 @@ did_status did_get_info(did_ctx* c, did_info* info) {
   info->sweep_kernel_ms = c->sweep_ms;
   info->dense_launches = c->dense_launches;
   info->dense_kernel_ms = c->dense_ms;
+  return DID_OK;
+}
+
+did_status did_get_phase_times(did_ctx* c, uint64_t* stamps, int32_t cap, int32_t* n) {
+  if (!c || cap < 0 || (cap > 0 && !stamps)) return DID_EINVAL;
+  const int have = 4 * c->tstamp_n;
+  if (n) *n = have;
+  const int m = std::min(have, cap);
+  if (m > 0) {
+    DID_CUDA(c, cudaMemcpyAsync(stamps, c->tstamp, sizeof(uint64_t) * m, cudaMemcpyDefault, c->stream));
+    DID_CUDA(c, cudaStreamSynchronize(c->stream));
+  }
   return DID_OK;
 }
 

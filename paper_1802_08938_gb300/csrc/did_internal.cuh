@@ -27,6 +27,7 @@ struct Ctrl {
   int err;             // device error word
   int stopped;         // 1 when the stopping rule held inside the launch
   int sweeps;          // sweeps completed by the launch
+  unsigned work[2];    // column-unit counters of alternate passes
 };
 
 // ------------------------------------------------------------ device helpers
@@ -73,6 +74,67 @@ __device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned target, int* e
   }
   __syncthreads();
   return s_ok != 0;
+}
+
+// ------------------------------------------------ TMA bulk copies + mbarrier
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+// Makes barrier initialisation visible to the async proxy (TMA).
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for phase `parity` of an mbarrier.  On expiry the error word is
+// set and the wait is retried once more with the same limit (the copy it
+// tracks may still be in flight); returns false if both ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* b, uint32_t parity, int* err, uint64_t timeout_ns) {
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    const uint64_t t0 = globaltimer_ns();
+    unsigned iters = 0;
+    while (true) {
+      if (mbar_try_wait(b, parity)) return attempt == 0;
+      if (++iters > (1u << 26) || globaltimer_ns() - t0 > timeout_ns) break;
+    }
+    atomicCAS(err, 0, kDevErrTimeout);
+  }
+  return false;
+}
+// 1-D bulk copy global -> shared (16-byte aligned addresses, size a multiple
+// of 16) completing on an mbarrier with a transaction count.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(b))
+      : "memory");
+}
+// Order this thread's generic-proxy accesses before later async-proxy ones.
+__device__ __forceinline__ void fence_proxy_async_shared() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
 // Named barrier over `nthreads` threads (a multiple of 32) with id 1..15.
@@ -177,15 +239,47 @@ __host__ __device__ __forceinline__ double u01_f64(uint64_t w) {
   return (double)(w >> 11) * 1.1102230246251565e-16;              // 2^-53
 }
 
+// Column range of unit u.  Dynamic units come in three tiers of TG units each
+// (TG = column groups in the grid), covering about 60%, 30% and 10% of the
+// columns: big units first, small ones last, so the groups that finish early
+// take the small units and the pass ends nearly together.  Static units: one
+// contiguous range per group.
+struct Units {
+  int64_t n0, n1;        // columns in tier 0 and tier 0+1
+  int64_t c0, c1, c2;    // unit widths of the tiers
+  int64_t tg;            // units per tier
+};
+__host__ __device__ __forceinline__ void unit_range(const Units& U, int64_t N, int64_t u, int64_t& lo, int64_t& hi) {
+  if (u < U.tg) {
+    lo = u * U.c0;
+    hi = lo + U.c0 < U.n0 ? lo + U.c0 : U.n0;
+  } else if (u < 2 * U.tg) {
+    lo = U.n0 + (u - U.tg) * U.c1;
+    hi = lo + U.c1 < U.n1 ? lo + U.c1 : U.n1;
+  } else {
+    lo = U.n1 + (u - 2 * U.tg) * U.c2;
+    hi = lo + U.c2 < N ? lo + U.c2 : N;
+  }
+  if (lo > N) lo = N;
+  if (hi > N) hi = N;
+}
+
+// Unit holding column j (inverse of unit_range).
+__host__ __device__ __forceinline__ int64_t unit_of(const Units& U, int64_t j) {
+  if (j < U.n0) return j / U.c0;
+  if (j < U.n1) return U.tg + (j - U.n0) / U.c1;
+  return 2 * U.tg + (j - U.n1) / U.c2;
+}
+
 // ------------------------------------------------------------ host launchers
 struct SweepArgs {
   void* R;            // ld x N residual (float or bf16)
   float* B;           // ld x K, column-major, rows >= M are zero
   float* C;           // K x N, row-major
-  float* P;           // [grid][ld] per-CTA partials of R c^T
-  double* CCp;        // [grid] per-CTA partials of ||c||^2
+  float* P;           // [nunits][ld] per-unit partials of R c^T
+  double* CCp;        // [nunits] per-unit partials of ||c||^2
   double* Sp;         // [grid][2] per-CTA partials of ||b'||^2 and b'.b
-  double* OBJp;       // [grid] per-CTA partials of sum R^2
+  double* OBJp;       // [nunits] per-unit partials of sum R^2
   float* bold;        // [ld] previous b_k while c_k is updated
   Ctrl* ctrl;         // barrier, error word, stop flag, sweep count
   double* trace;      // trace[s] = objective after sweep s of this launch
@@ -193,6 +287,12 @@ struct SweepArgs {
   int64_t N;
   int M, ld, K;
   int GS, NG;         // threads per column group, groups per CTA
+  int D;              // shared-memory stages (columns in flight) per group
+  Units units;        // column ranges of the units
+  int nunits;         // units per pass
+  int dynamic;        // 1: groups take units from a counter, partials per unit;
+                      // 0: group g takes unit g, partials per CTA
+  int npart;          // partial rows the b-reduce adds (nunits or grid)
   int n_sweeps;       // sweeps of this launch
   int prologue;       // 1: first form the partials of R c_1^T from R
   double f_prev;      // objective before the first sweep of this launch
@@ -202,16 +302,22 @@ struct SweepArgs {
   int order;          // did_order
   int bar_extra;      // test hook: extra arrivals each grid wait expects
   uint64_t timeout_ns;
+  uint64_t* tstamp;   // optional phase stamps (CTA 0), 4 per k; nullptr = off
+  int tstamp_cap;     // number of k-steps that fit in tstamp
 };
 
 struct SweepPlan {
-  int grid, GS, NG, NR;
+  int grid, GS, NG, NR, D;
+  Units units;
+  int nunits, dynamic, npart;
   size_t smem;
   const void* func;
 };
 
 // Choose the column-group shape and grid for (ld, precision); fills *plan.
-did_status plan_sweep(int ld, bool bf16, int grid_override, SweepPlan* plan, char* err, size_t errlen);
+// max_units: upper bound on units the caller's partial buffers hold (0 = no bound).
+did_status plan_sweep(int ld, int64_t N, bool bf16, int grid_override, int64_t max_units, SweepPlan* plan,
+                      char* err, size_t errlen);
 cudaError_t launch_sweep(const SweepPlan& plan, const SweepArgs& args, cudaStream_t s);
 
 // Dense pass over tiles of X - B C:

@@ -35,6 +35,9 @@ namespace {
 
 enum PassMode { kPrologue = 0, kUpdateC = 1 };
 
+constexpr int kMaxNrF32 = 10;   // 16-byte vectors per thread and column
+constexpr int kMaxNrBf16 = 5;
+
 // Sum v over the GS threads of a column group; every thread of the group gets
 // the same value (xor tree within warps, then the warps' totals in order).
 __device__ __forceinline__ float group_sum(float v, int GS, int g, int lt, float* red, int parity) {
@@ -49,182 +52,395 @@ __device__ __forceinline__ float group_sum(float v, int GS, int g, int lt, float
   return s;
 }
 
-template <int NR, bool BF16>
-struct Column {
-  typedef Vec<BF16> V;
-  static constexpr int VR = V::kRows;
-  typedef typename V::raw raw;
+// float64 sum over the GS threads of a column group (same scheme as group_sum).
+__device__ __forceinline__ double group_sum_f64(double v, int GS, int g, int lt, double* redd) {
+  v = warp_sum_f64(v);
+  if (GS <= 32) return v;
+  double* slot = redd + g * 16;
+  if ((lt & 31) == 0) slot[lt >> 5] = v;
+  named_bar(1 + g, GS);
+  double s = 0.0;
+  for (int i = 0; i < (GS >> 5); ++i) s += slot[i];
+  named_bar(1 + g, GS);   // slots free for the next call
+  return s;
+}
 
-  __device__ __forceinline__ static void load(raw* dst, const raw* col, int lt, int GS, int nvec) {
-#pragma unroll
-    for (int r = 0; r < NR; ++r) {
-      const int q = lt + r * GS;
-      if (q < nvec) {
-        dst[r] = __ldcs(col + q);
-      } else {
-        dst[r] = raw();
-      }
-    }
-  }
+// Shared memory of a sweep CTA (byte offsets; the same formula on host and
+// device).  ring: per column group, D stages of one column each, filled by
+// TMA bulk copies; it is reused for the per-group partials at the end of a
+// pass (NG x ld floats, which fit because D x sizeof(elem) >= 4).
+struct SweepSmem {
+  size_t bo, bnw, ring, red, redd, dscr, bc, meta, mbar, total;
+};
+__host__ __device__ __forceinline__ size_t align128(size_t x) { return (x + 127) & ~(size_t)127; }
+__host__ __device__ __forceinline__ SweepSmem sweep_smem(int ld, int NG, int D, int elem_bytes) {
+  SweepSmem L;
+  size_t o = 0;
+  L.bo = o;   o += align128((size_t)ld * sizeof(float));
+  L.bnw = o;  o += elem_bytes == 2 ? align128((size_t)ld * sizeof(float)) : 0;   // BF16: b_k' planes
+  L.ring = o; o += align128((size_t)NG * D * ld * elem_bytes);
+  L.red = o;  o += 512 * sizeof(float);
+  L.redd = o; o += 16 * 16 * sizeof(double);
+  L.dscr = o; o += kWarps * sizeof(double);
+  L.bc = o;   o += 4 * sizeof(double);
+  L.meta = o; o += (size_t)NG * D * sizeof(int64_t);
+  L.mbar = o; o += (size_t)NG * D * sizeof(uint64_t);
+  L.total = o;
+  return L;
+}
+
+struct SmemPtrs {
+  float* bo;              // previous b_k (kUpdateC)
+  float* bnw;             // b_k' (BF16 residual: kept here instead of registers)
+  unsigned char* ring;    // column stages
+  float* red;             // group reduction slots / b-reduce scratch
+  double* redd;           // group float64 reduction slots
+  double* dscr;           // block_sum_f64 scratch
+  double* bc;             // broadcast scalars
+  int64_t* meta;          // column index held by each stage (-1: end of stream)
+  uint64_t* mbar;         // one mbarrier per stage
 };
 
-// One pass over the columns this CTA owns.
-//   kPrologue: p += R c_knext^T, cc += ||c_knext||^2, no store.
-//   kUpdateC:  c_k update, R write-back, p for knext (if knext >= 0), obj.
-// sb[0..ld) holds b_k', sb[ld..2ld) holds the previous b_k (kUpdateC).
-template <int NR, bool BF16>
-__device__ __forceinline__ void column_pass(const SweepArgs& a, int k, int knext, int mode, bool want_obj,
-                                            float inv_bb, float alpha, bool cdeg, float* sb, float* red,
-                                            double* dscr) {
-  typedef Column<NR, BF16> Col;
-  typedef typename Col::raw raw;
-  typedef typename Col::V V;
-  constexpr int VR = Col::VR;
+// One pass over all columns.
+//   kPrologue: partials of R c_knext^T and ||c_knext||^2, no store.
+//   kUpdateC:  c_k update, R write-back, partials for knext, and (OBJ) sum R^2.
+// Columns come in units (contiguous ranges of `ch` columns).  A column group
+// takes units one at a time -- from a grid-wide counter when a.dynamic, else
+// the unit with its own index -- and writes each unit's partials to that
+// unit's slot, so the grid reduction that follows is the same whichever group
+// took which unit.  The group's first thread streams the unit's columns into
+// a ring of D shared-memory stages by TMA bulk copies, each stage tagged with
+// its column index (-1 closes the stream); a stage is refilled once every
+// thread of the group has passed the next column's reduction.  `it` counts
+// the stages this group has consumed since the launch (stage and phase).
+// Vector slots r < NR-1 are always inside the column (NR = ceil(nvec / GS));
+// only the last slot needs a bounds test.
+template <int NR, bool BF16, int MODE, bool OBJ>
+__device__ __forceinline__ void column_pass(const SweepArgs& a, int k, int knext, float inv_bb, float alpha,
+                                            bool cdeg, const SmemPtrs& sm, unsigned& it, int pass) {
+  typedef Vec<BF16> V;
+  typedef typename V::raw raw;
+  constexpr int VR = V::kRows;
+  constexpr int VH = VR / 2;       // float2 pairs per vector
+  constexpr int ELEM = BF16 ? 2 : 4;
 
-  const int GS = a.GS;
-  const int nvec = a.ld / VR;
+  const int GS = a.GS, D = a.D, ld = a.ld;
+  const int nvec = ld / VR;
   const int g = threadIdx.x / GS;
   const int lt = threadIdx.x - g * GS;
-  const int64_t TG = (int64_t)gridDim.x * a.NG;
   const int64_t N = a.N;
-  raw* Rv = reinterpret_cast<raw*>(a.R);
-  const float* bnew = sb;
-  const float* bprev = sb + a.ld;
+  const Units UN = a.units;
+  const int nunits = a.nunits;
+  const uint32_t colbytes = (uint32_t)ld * ELEM;
+  const uint64_t timeout_ns = a.timeout_ns;
+  int* err = &a.ctrl->err;
+  unsigned* work = &a.ctrl->work[pass & 1];
+  float* Cw = a.C + (int64_t)k * N;
+  const unsigned char* Rbytes = reinterpret_cast<const unsigned char*>(a.R);
+  unsigned char* ring = sm.ring + (size_t)g * D * colbytes;
+  uint64_t* bars = sm.mbar + g * D;
+  volatile int64_t* meta = sm.meta + g * D;
+  const bool last_ok = lt + (NR - 1) * GS < nvec;       // the last slot of this thread is in range
+  const float* bo_base = sm.bo;
+  const int half = ld / 2;
+  const int gg = blockIdx.x * a.NG + g;
 
-  float p[NR][VR];
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.ctrl->work[(pass + 1) & 1] = 0u;   // next pass's counter
+
+  // b_k' for this thread's rows: registers for an FP32 residual; for a BF16
+  // residual (twice the rows per vector) it is read from shared memory.
+  constexpr int NRB = BF16 ? 1 : NR;
+  float2 bn[NRB][VH];
+  float2 p[NR][VH];    // partials of R c_knext^T for this thread's rows (current unit)
 #pragma unroll
-  for (int r = 0; r < NR; ++r)
+  for (int r = 0; r < NR; ++r) {
+    const int q = lt + r * GS;
+    const bool ok = r < NR - 1 || last_ok;
 #pragma unroll
-    for (int e = 0; e < VR; ++e) p[r][e] = 0.f;
+    for (int e = 0; e < VR; e += 4) {
+      if (!BF16) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (MODE == kUpdateC && ok) v = __ldcg(reinterpret_cast<const float4*>(a.B + (size_t)k * ld + q * VR + e));
+        bn[BF16 ? 0 : r][e / 2] = make_float2(v.x, v.y);
+        bn[BF16 ? 0 : r][e / 2 + 1] = make_float2(v.z, v.w);
+      }
+      p[r][e / 2] = make_float2(0.f, 0.f);
+      p[r][e / 2 + 1] = make_float2(0.f, 0.f);
+    }
+  }
+  // b_k' of vector slot r, four values e0..e0+3 (FP32: registers; BF16: one
+  // 16-byte load from a shared half plane).
+  const float* bn_base = sm.bnw;
+  auto bn_quad = [&](int r, int e0, float2& lo, float2& hi) {
+    if (!BF16) {
+      lo = bn[BF16 ? 0 : r][e0 / 2];
+      hi = bn[BF16 ? 0 : r][e0 / 2 + 1];
+      return;
+    }
+    const int q = lt + r * GS;
+    const float4 t = *reinterpret_cast<const float4*>(bn_base + (e0 / 4) * half + q * 4);
+    lo = make_float2(t.x, t.y);
+    hi = make_float2(t.z, t.w);
+  };
   double cc_acc = 0.0, obj_acc = 0.0;
   int parity = 0;
 
-  int64_t j = (int64_t)blockIdx.x * a.NG + g;
-  raw cur[NR], nxt[NR];
-  if (j < N) Col::load(cur, Rv + j * nvec, lt, GS, nvec);
-  for (; j < N; j += TG) {
-    const int64_t jn = j + TG;
-    if (jn < N) Col::load(nxt, Rv + jn * nvec, lt, GS, nvec);
+  // Producer state (used by the group's first thread only).
+  int64_t pj = 0, pend = 0;
+  bool pdone = false, pclosed = false, pstatic_taken = false;
+  auto next_col = [&]() -> int64_t {
+    while (!pdone) {
+      if (pj < pend) return pj++;
+      int64_t u;
+      if (a.dynamic) {
+        u = (int64_t)atomicAdd(work, 1u);
+      } else {
+        u = pstatic_taken ? nunits : gg;
+        pstatic_taken = true;
+      }
+      if (u >= nunits) { pdone = true; break; }
+      unit_range(UN, N, u, pj, pend);
+    }
+    return -1;
+  };
+  auto issue = [&](unsigned st) {   // fills stage st with the next column, or closes the stream once
+    if (pclosed) return;
+    const int64_t jn = next_col();
+    meta[st] = jn;
+    if (jn >= 0) {
+      mbar_arrive_expect_tx(bars + st, colbytes);
+      bulk_load(ring + (size_t)st * colbytes, Rbytes + (size_t)jn * colbytes, colbytes, bars + st);
+    } else {
+      mbar_arrive(bars + st);
+      pclosed = true;
+    }
+  };
+  if (lt == 0) {
+    fence_proxy_async_shared();   // the ring was last written by generic stores
+    for (int i = 0; i < D && !pclosed; ++i) issue((it + (unsigned)i) % D);
+  }
 
-    float f[NR][VR];
+  // Consumer state (every thread of the group).
+  int64_t cu = -1, cu_lo = 0, cu_hi = 0;   // unit being consumed and its column range
+  const float* Ck = Cw;
+  const float* Cn = a.C + (int64_t)knext * N;
+  float co0 = 0.f, co1 = 0.f, cn0 = 0.f, cn1 = 0.f;
+  int64_t pf_j = -1;                        // column the prefetched co0/cn0 belong to
+
+  auto flush = [&](int64_t u) {             // unit partials -> slot u (dynamic units)
+    if (u < 0 || !a.dynamic) return;
+    float* Pu = a.P + (size_t)u * ld;
 #pragma unroll
-    for (int r = 0; r < NR; ++r) V::unpack(cur[r], f[r]);
+    for (int r = 0; r < NR; ++r) {
+      const int q = lt + r * GS;
+      if (r < NR - 1 || last_ok) {
+#pragma unroll
+        for (int e = 0; e < VR; e += 4)
+          __stcg(reinterpret_cast<float4*>(Pu + q * VR + e),
+                 make_float4(p[r][e / 2].x, p[r][e / 2].y, p[r][e / 2 + 1].x, p[r][e / 2 + 1].y));
+      }
+#pragma unroll
+      for (int h = 0; h < VH; ++h) p[r][h] = make_float2(0.f, 0.f);
+    }
+    if (lt == 0) __stcg(a.CCp + u, cc_acc);
+    cc_acc = 0.0;
+    if (OBJ) {
+      const double o = group_sum_f64(obj_acc, GS, g, lt, sm.redd);
+      if (lt == 0) __stcg(a.OBJp + u, o);
+      obj_acc = 0.0;
+    }
+  };
 
-    const float c_old = (mode == kUpdateC) ? __ldcg(a.C + (int64_t)k * N + j) : 0.f;
+  for (int64_t i = 0;; ++i) {
+    const unsigned st = it % D;
+    mbar_wait_bounded(bars + st, (it / D) & 1u, err, timeout_ns);
+    const int64_t j = meta[st];
+    ++it;
+    if (j < 0) break;
+    if (j < cu_lo || j >= cu_hi) {          // first column of a new unit
+      flush(cu);
+      cu = unit_of(UN, j);
+      unit_range(UN, N, cu, cu_lo, cu_hi);
+    }
+    if (j != pf_j) {                        // no prefetch for this column (a unit's start)
+      if (MODE == kUpdateC) co0 = __ldcg(Ck + j);
+      cn0 = __ldcg(Cn + j);
+      if (j + 1 < cu_hi) {
+        if (MODE == kUpdateC) co1 = __ldcg(Ck + j + 1);
+        cn1 = __ldcg(Cn + j + 1);
+      }
+    }
+    const float c_old = co0;
+    const float c_nx = cn0;
+    co0 = co1;
+    cn0 = cn1;
+    if (j + 2 < cu_hi) {                    // c_kj and c_{knext,j} two columns ahead
+      if (MODE == kUpdateC) co1 = __ldcg(Ck + j + 2);
+      cn1 = __ldcg(Cn + j + 2);
+    }
+    pf_j = j + 1;
+    // Once every thread of the group has passed this column's reduction (or
+    // barrier), all of them are done with the previous stage: refill it.
+    auto refill_prev = [&]() {
+      if (lt == 0 && i >= 1) {
+        fence_proxy_async_shared();
+        issue((it + D - 2) % D);            // the stage consumed one iteration ago
+      }
+    };
+    const raw* stage = reinterpret_cast<const raw*>(ring + (size_t)st * colbytes) + lt;
+    raw* Rcol = reinterpret_cast<raw*>(a.R) + j * nvec + lt;
+
     float c_new = c_old;
-    if (mode == kUpdateC) {
-      float d = 0.f;
+    if (MODE == kUpdateC) {
+      float2 d2 = make_float2(0.f, 0.f);
 #pragma unroll
       for (int r = 0; r < NR; ++r) {
-        const int q = lt + r * GS;
-        if (q < nvec) {
+        if (r < NR - 1 || last_ok) {
+          float f[VR];
+          V::unpack(stage[r * GS], f);
 #pragma unroll
-          for (int e = 0; e < VR; ++e) d = fmaf(bnew[q * VR + e], f[r][e], d);
+          for (int e = 0; e < VR; e += 4) {
+            float2 blo, bhi;
+            bn_quad(r, e, blo, bhi);
+            d2 = __ffma2_rn(blo, make_float2(f[e], f[e + 1]), d2);
+            d2 = __ffma2_rn(bhi, make_float2(f[e + 2], f[e + 3]), d2);
+          }
         }
       }
-      const float dot = group_sum(d, GS, g, lt, red, parity);
+      const float dot = group_sum(d2.x + d2.y, GS, g, lt, sm.red, parity);
       parity ^= 1;
+      refill_prev();
       if (!cdeg) {
         const float t = fmaf(alpha, c_old, dot * inv_bb);
         c_new = t > 0.f ? t : 0.f;
       }
-      if (lt == 0) __stcg(a.C + (int64_t)k * N + j, c_new);
-#pragma unroll
-      for (int r = 0; r < NR; ++r) {
-        const int q = lt + r * GS;
-        if (q < nvec) {
-#pragma unroll
-          for (int e = 0; e < VR; ++e)
-            f[r][e] = fmaf(bprev[q * VR + e], c_old, fmaf(-bnew[q * VR + e], c_new, f[r][e]));
-          __stcs(Rv + j * nvec + q, V::pack(f[r]));
-        }
-      }
-      if (BF16) {
-        // The stored residual is the rounded value: continue from it.
-#pragma unroll
-        for (int r = 0; r < NR; ++r) {
-          raw t = V::pack(f[r]);
-          V::unpack(t, f[r]);
-        }
-      }
+      if (lt == 0) __stcg(Cw + j, c_new);
+    } else {
+      if (GS > 32) named_bar(1 + g, GS); else __syncwarp();
+      refill_prev();
     }
-    if (knext >= 0) {
-      const float cn = (knext == k && mode == kUpdateC) ? c_new : __ldcg(a.C + (int64_t)knext * N + j);
-#pragma unroll
-      for (int r = 0; r < NR; ++r)
-#pragma unroll
-        for (int e = 0; e < VR; ++e) p[r][e] = fmaf(f[r][e], cn, p[r][e]);
-      if (lt == 0) cc_acc += (double)cn * (double)cn;
-    }
-    if (want_obj) {
-      float s = 0.f;
-#pragma unroll
-      for (int r = 0; r < NR; ++r)
-#pragma unroll
-        for (int e = 0; e < VR; ++e) s = fmaf(f[r][e], f[r][e], s);
-      obj_acc += (double)s;
-    }
-#pragma unroll
-    for (int r = 0; r < NR; ++r) cur[r] = nxt[r];
-  }
+    const float cn = (knext == k && MODE == kUpdateC) ? c_new : c_nx;
+    const float2 co2 = make_float2(c_old, c_old);
+    const float2 mcn2 = make_float2(-c_new, -c_new);
+    const float2 cn2 = make_float2(cn, cn);
 
-  if (knext >= 0) {
-    // Partials of R c_knext^T: groups -> shared memory -> CTA row sums in order.
-    float* pg = sb;                       // aliases b_k' / b_k: done with them
+    // Second read of the stage: update, store, accumulate.
+    float2 s2 = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      if (r < NR - 1 || last_ok) {
+        const int q = lt + r * GS;
+        float f[VR];
+        V::unpack(stage[r * GS], f);
+        if (MODE == kUpdateC) {
+#pragma unroll
+          for (int e = 0; e < VR; e += 4) {
+            // BF16: the 8 previous-b values of vector q are stored as two
+            // float4 half planes, so a warp's loads are contiguous 16-byte runs.
+            const float4 t =
+                *reinterpret_cast<const float4*>(bo_base + (BF16 ? (e / 4) * half + q * 4 : q * VR + e));
+            float2 blo, bhi;
+            bn_quad(r, e, blo, bhi);
+            float2 lo = __ffma2_rn(blo, mcn2, make_float2(f[e], f[e + 1]));
+            float2 hi = __ffma2_rn(bhi, mcn2, make_float2(f[e + 2], f[e + 3]));
+            lo = __ffma2_rn(make_float2(t.x, t.y), co2, lo);
+            hi = __ffma2_rn(make_float2(t.z, t.w), co2, hi);
+            f[e] = lo.x; f[e + 1] = lo.y; f[e + 2] = hi.x; f[e + 3] = hi.y;
+          }
+          __stcs(Rcol + r * GS, V::pack(f));
+        }
+#pragma unroll
+        for (int h = 0; h < VH; ++h) {
+          const float2 fv = make_float2(f[2 * h], f[2 * h + 1]);
+          p[r][h] = __ffma2_rn(fv, cn2, p[r][h]);
+          if (OBJ) s2 = __ffma2_rn(fv, fv, s2);
+        }
+      }
+    }
+    if (lt == 0) cc_acc += (double)cn * (double)cn;
+    if (OBJ) obj_acc += (double)(s2.x + s2.y);
+  }
+  flush(cu);
+  // R written here is read by TMA (async proxy) in the next pass.
+  if (MODE == kUpdateC) fence_proxy_async_global();
+
+  if (!a.dynamic) {
+    // Static units: partials per CTA -- groups -> shared memory -> row sums in
+    // group order (the ring is free: every copy of this pass was consumed).
+    float* pg = reinterpret_cast<float*>(sm.ring);
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
       const int q = lt + r * GS;
-      if (q < nvec) {
+      if (r < NR - 1 || last_ok) {
 #pragma unroll
         for (int e = 0; e < VR; e += 4)
-          *reinterpret_cast<float4*>(pg + (size_t)g * a.ld + q * VR + e) =
-              make_float4(p[r][e], p[r][e + 1], p[r][e + 2], p[r][e + 3]);
+          *reinterpret_cast<float4*>(pg + (size_t)g * ld + q * VR + e) =
+              make_float4(p[r][e / 2].x, p[r][e / 2].y, p[r][e / 2 + 1].x, p[r][e / 2 + 1].y);
       }
     }
     __syncthreads();
-    float* Pc = a.P + (size_t)blockIdx.x * a.ld;
-    for (int idx = threadIdx.x; idx < a.ld; idx += blockDim.x) {
-      float s = 0.f;
-      for (int gi = 0; gi < a.NG; ++gi) s += pg[(size_t)gi * a.ld + idx];
-      __stcg(Pc + idx, s);
+    float* Pc = a.P + (size_t)blockIdx.x * ld;
+    for (int idx = threadIdx.x; idx < ld; idx += blockDim.x) {
+      float sum = 0.f;
+      for (int gi = 0; gi < a.NG; ++gi) sum += pg[(size_t)gi * ld + idx];
+      __stcg(Pc + idx, sum);
     }
-    const double cc = block_sum_f64(cc_acc, dscr);
+    const double cc = block_sum_f64(cc_acc, sm.dscr);
     if (threadIdx.x == 0) __stcg(a.CCp + blockIdx.x, cc);
-  }
-  if (want_obj) {
-    const double o = block_sum_f64(obj_acc, dscr);
-    if (threadIdx.x == 0) __stcg(a.OBJp + blockIdx.x, o);
+    if (OBJ) {
+      const double o = block_sum_f64(obj_acc, sm.dscr);
+      if (threadIdx.x == 0) __stcg(a.OBJp + blockIdx.x, o);
+    }
+    __syncthreads();   // the ring is free again before the next pass primes it
   }
 }
 
-// b-reduce for block k: s = sum over CTAs of P (fixed order), b_k' from the
-// closed form, ||b_k'||^2 and b_k'.b_k partials of this CTA's row slice.
+// b-reduce for block k: s = sum over the partial rows of P (fixed order), b_k'
+// from the closed form, ||b_k'||^2 and b_k'.b_k partials of this CTA's row
+// slice.  The slice's rows are spread over the CTA's threads together with
+// interleaved subsets of the partial rows (up to 16 loads in flight each);
+// the subsets' sums are added in subset order.
 __device__ __forceinline__ void b_reduce(const SweepArgs& a, int k, float* acc, double* bc) {
   const int G = gridDim.x;
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int U = a.npart;
   if (w == 0) {
-    const double cc = warp_sum_global_f64(a.CCp, G, 1);
+    const double cc = warp_sum_global_f64(a.CCp, U, 1);
     if (l == 0) bc[0] = cc;
   }
-  __syncthreads();
-  const double cc = bc[0];
   const int rpc = (a.ld + G - 1) / G;
   const int r0 = blockIdx.x * rpc;
   const int r1 = min(a.ld, r0 + rpc);
+  const int nrows = max(0, r1 - r0);
   double bb = 0.0, bob = 0.0;
-  for (int c0 = r0; c0 < r1; c0 += 32) {
-    const int row = c0 + l;
+  // rows handled per round: at most 32 (one per lane of warp 0 in the epilogue)
+  for (int c0 = 0; c0 < nrows; c0 += 32) {
+    const int rows = min(32, nrows - c0);
+    const int lanes = kSweepThreads / rows;          // subsets per row (>= 16)
+    const int t = threadIdx.x;
+    const int rr = t % rows, sub = t / rows;
     float s = 0.f;
-    if (row < r1) {
-#pragma unroll 4
-      for (int gi = w; gi < G; gi += kWarps) s += __ldcg(a.P + (size_t)gi * a.ld + row);
+    if (sub < lanes) {
+      const int row = r0 + c0 + rr;
+      for (int gi0 = sub; gi0 < U; gi0 += 16 * lanes) {
+        float v[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int gi = gi0 + u * lanes;
+          v[u] = gi < U ? __ldcg(a.P + (size_t)gi * a.ld + row) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 16; ++u) s += v[u];
+      }
     }
-    acc[w * 32 + l] = s;
+    acc[t] = s;                                       // acc[sub * rows + rr]
     __syncthreads();
-    if (w == 0 && row < r1) {
+    const double cc = bc[0];
+    if (w == 0 && l < rows) {
+      const int row = r0 + c0 + l;
       float tot = 0.f;
-      for (int ww = 0; ww < kWarps; ++ww) tot += acc[ww * 32 + l];
+      for (int sb = 0; sb < lanes; ++sb) tot += acc[sb * rows + l];
       const float b_old = __ldcg(a.B + (size_t)k * a.ld + row);
       float b_new = b_old;
       if (cc > 0.0) {
@@ -238,6 +454,8 @@ __device__ __forceinline__ void b_reduce(const SweepArgs& a, int k, float* acc, 
     }
     __syncthreads();
   }
+  __syncthreads();
+  const double cc = bc[0];
   if (w == 0) {
     bb = warp_sum_f64(bb);
     bob = warp_sum_f64(bob);
@@ -251,15 +469,28 @@ __device__ __forceinline__ void b_reduce(const SweepArgs& a, int k, float* acc, 
 
 template <int NR, bool BF16>
 __global__ void __launch_bounds__(kSweepThreads, 1) sweep_kernel(SweepArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* sb = reinterpret_cast<float*>(smem_raw);
-  const size_t uni = max((size_t)max(2, a.NG) * a.ld, (size_t)512);
-  float* red = sb + uni;                               // [2][16][16]
-  double* dscr = reinterpret_cast<double*>(red + 512); // [kWarps]
-  double* bc = dscr + kWarps;                          // [4]
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const SweepSmem L = sweep_smem(a.ld, a.NG, a.D, BF16 ? 2 : 4);
+  SmemPtrs sm;
+  sm.bo = reinterpret_cast<float*>(smem_raw + L.bo);
+  sm.bnw = reinterpret_cast<float*>(smem_raw + L.bnw);
+  sm.ring = smem_raw + L.ring;
+  sm.red = reinterpret_cast<float*>(smem_raw + L.red);
+  sm.redd = reinterpret_cast<double*>(smem_raw + L.redd);
+  sm.meta = reinterpret_cast<int64_t*>(smem_raw + L.meta);
+  sm.dscr = reinterpret_cast<double*>(smem_raw + L.dscr);
+  sm.bc = reinterpret_cast<double*>(smem_raw + L.bc);
+  sm.mbar = reinterpret_cast<uint64_t*>(smem_raw + L.mbar);
+  double* bc = sm.bc;
   const int G = gridDim.x;
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   unsigned nbar = 0;
+  unsigned it = 0;     // stages consumed by this thread's column group
+  int pass = 0;        // column passes of this launch (selects the unit counter)
+
+  if (threadIdx.x < a.NG * a.D) mbar_init(sm.mbar + threadIdx.x, 1);
+  fence_mbar_init();
+  __syncthreads();
 
 #define DID_GRID_SYNC()                                                                  \
   do {                                                                                   \
@@ -270,24 +501,35 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_kernel(SweepArgs a) {
   } while (0)
 
   if (a.prologue) {
-    column_pass<NR, BF16>(a, 0, 0, kPrologue, false, 0.f, 0.f, true, sb, red, dscr);
+    column_pass<NR, BF16, kPrologue, false>(a, 0, 0, 0.f, 0.f, true, sm, it, pass++);
     DID_GRID_SYNC();
   }
   const double f0 = a.f0;
   double f_prev = a.f_prev;
 
+  const bool stamps = a.tstamp != nullptr && blockIdx.x == 0 && threadIdx.x == 0;
   for (int s = 0; s < a.n_sweeps; ++s) {
     for (int k = 0; k < a.K; ++k) {
-      b_reduce(a, k, sb, bc);
+      const int step = s * a.K + k;
+      const bool rec = stamps && step < a.tstamp_cap;
+      if (rec) a.tstamp[4 * step + 0] = globaltimer_ns();
+      b_reduce(a, k, sm.red, bc);
       DID_GRID_SYNC();
+      if (rec) a.tstamp[4 * step + 1] = globaltimer_ns();
       if (w == 0) {
         const double bb = warp_sum_global_f64(a.Sp, G, 2);
         const double bob = warp_sum_global_f64(a.Sp + 1, G, 2);
         if (l == 0) { bc[1] = bb; bc[2] = bob; }
       }
-      for (int i = threadIdx.x; i < a.ld; i += blockDim.x) {
-        sb[i] = __ldcg(a.B + (size_t)k * a.ld + i);
-        sb[a.ld + i] = __ldcg(a.bold + i);
+      if (BF16) {
+        // half planes: element e of 8-row vector q -> (e/4)*ld/2 + q*4 + e%4
+        for (int i = threadIdx.x; i < a.ld; i += blockDim.x) {
+          const int dst = ((i & 7) >> 2) * (a.ld / 2) + (i >> 3) * 4 + (i & 3);
+          sm.bo[dst] = __ldcg(a.bold + i);
+          sm.bnw[dst] = __ldcg(a.B + (size_t)k * a.ld + i);
+        }
+      } else {
+        for (int i = threadIdx.x; i < a.ld; i += blockDim.x) sm.bo[i] = __ldcg(a.bold + i);
       }
       __syncthreads();
       const double bb = bc[1], bob = bc[2];
@@ -296,11 +538,16 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_kernel(SweepArgs a) {
       const float alpha = cdeg ? 0.f : (float)(bob / bb);
       if (cdeg && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(a.degen, 1ull);
       const int knext = (k + 1 < a.K) ? k + 1 : 0;
-      column_pass<NR, BF16>(a, k, knext, kUpdateC, k == a.K - 1, inv_bb, alpha, cdeg, sb, red, dscr);
+      if (k == a.K - 1)
+        column_pass<NR, BF16, kUpdateC, true>(a, k, knext, inv_bb, alpha, cdeg, sm, it, pass++);
+      else
+        column_pass<NR, BF16, kUpdateC, false>(a, k, knext, inv_bb, alpha, cdeg, sm, it, pass++);
+      if (rec) a.tstamp[4 * step + 2] = globaltimer_ns();
       DID_GRID_SYNC();
+      if (rec) a.tstamp[4 * step + 3] = globaltimer_ns();
     }
     if (w == 0) {
-      const double o = warp_sum_global_f64(a.OBJp, G, 1);
+      const double o = warp_sum_global_f64(a.OBJp, a.npart, 1);
       if (l == 0) bc[3] = 0.5 * o;
     }
     __syncthreads();
@@ -340,6 +587,8 @@ const void* pick_func(bool bf16, int NR) {
       case 6: return sweep_func<6, false>();
       case 7: return sweep_func<7, false>();
       case 8: return sweep_func<8, false>();
+      case 9: return sweep_func<9, false>();
+      case 10: return sweep_func<10, false>();
     }
   } else {
     switch (NR) {
@@ -348,7 +597,6 @@ const void* pick_func(bool bf16, int NR) {
       case 3: return sweep_func<3, true>();
       case 4: return sweep_func<4, true>();
       case 5: return sweep_func<5, true>();
-      case 6: return sweep_func<6, true>();
     }
   }
   return nullptr;
@@ -356,22 +604,33 @@ const void* pick_func(bool bf16, int NR) {
 
 }  // namespace
 
-size_t sweep_smem_bytes(int ld, int NG) {
-  const size_t uni = std::max((size_t)std::max(2, NG) * ld, (size_t)512);
-  return uni * sizeof(float) + 512 * sizeof(float) + (kWarps + 4) * sizeof(double);
-}
-
-did_status plan_sweep(int ld, bool bf16, int grid_override, SweepPlan* plan, char* err, size_t errlen) {
+did_status plan_sweep(int ld, int64_t N, bool bf16, int grid_override, int64_t max_units, SweepPlan* plan,
+                      char* err, size_t errlen) {
   const int VR = bf16 ? 8 : 4;
+  const int elem = bf16 ? 2 : 4;
   const int nvec = ld / VR;
-  const int nr_max = bf16 ? 6 : 8;
-  int best_gs = 0, best_nr = 0, best_waste = 1 << 30;
+  const int nr_max = bf16 ? kMaxNrBf16 : kMaxNrF32;
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const size_t budget = (size_t)optin - 1024;   // static shared memory of the kernel is < 1 KB
+  // Candidate shapes: GS threads per column group, NR vectors per thread.  More
+  // groups per CTA means more columns being reduced at once (latency hiding);
+  // a ring of at least 3 stages keeps 2 columns in flight per group.  Among
+  // shapes with at most 1/8 idle lanes and a 3-stage ring, take the most
+  // groups; otherwise the least idle lanes.
+  int best_gs = 0, best_nr = 0;
+  long best_key = -1;
   for (int GS = 32; GS <= kSweepThreads; GS *= 2) {
     int NR = (nvec + GS - 1) / GS;
     if (NR < 1) NR = 1;
     if (NR > nr_max) continue;
+    const int NG = kSweepThreads / GS;
     const int waste = GS * NR - nvec;
-    if (waste < best_waste) { best_waste = waste; best_gs = GS; best_nr = NR; }
+    const bool fits3 = sweep_smem(ld, NG, 3, elem).total <= budget;
+    const bool good = fits3 && waste * 8 <= GS * NR;
+    const long key = good ? (1L << 40) + ((long)NG << 20) - waste : (long)(1 << 20) - waste;
+    if (key > best_key) { best_key = key; best_gs = GS; best_nr = NR; }
   }
   if (best_gs == 0) {
     snprintf(err, errlen, "M too large for the sweep kernel: ld=%d exceeds %d rows", ld,
@@ -382,17 +641,10 @@ did_status plan_sweep(int ld, bool bf16, int grid_override, SweepPlan* plan, cha
   plan->NR = best_nr;
   plan->NG = kSweepThreads / best_gs;
   plan->func = pick_func(bf16, best_nr);
-  plan->smem = sweep_smem_bytes(ld, plan->NG);
-  if (plan->smem > 227 * 1024) {
-    snprintf(err, errlen, "sweep shared memory %zu bytes exceeds the per-CTA limit", plan->smem);
-    return DID_E_TOO_LARGE;
-  }
   // The cap is a property of the kernel function shared by every context: set
   // it to the device maximum (not to this plan's size), so that plans with
   // different ld on the same kernel variant can all launch.
-  int dev = 0, sms = 0, per_sm = 0, optin = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  int sms = 0, per_sm = 0;
   cudaFuncAttributes fa{};
   cudaError_t e = cudaFuncGetAttributes(&fa, plan->func);
   if (e == cudaSuccess)
@@ -402,10 +654,16 @@ did_status plan_sweep(int ld, bool bf16, int grid_override, SweepPlan* plan, cha
     snprintf(err, errlen, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
     return DID_ECUDA;
   }
-  if (plan->smem + fa.sharedSizeBytes > (size_t)optin) {
-    snprintf(err, errlen, "sweep shared memory %zu bytes exceeds the per-CTA limit", plan->smem);
+  // Deepest ring (2..6 stages per group) that fits the shared memory.
+  plan->D = 0;
+  for (int D = 6; D >= 2; --D) {
+    if (sweep_smem(ld, plan->NG, D, elem).total <= budget) { plan->D = D; break; }
+  }
+  if (plan->D == 0) {
+    snprintf(err, errlen, "sweep shared memory for ld=%d exceeds the per-CTA limit", ld);
     return DID_E_TOO_LARGE;
   }
+  plan->smem = sweep_smem(ld, plan->NG, plan->D, elem).total;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan->func, kSweepThreads, plan->smem);
   if (e != cudaSuccess || per_sm < 1) {
@@ -414,6 +672,36 @@ did_status plan_sweep(int ld, bool bf16, int grid_override, SweepPlan* plan, cha
   }
   const int max_grid = sms * per_sm;
   plan->grid = grid_override > 0 ? std::min(grid_override, max_grid) : max_grid;
+  // Column units.  SMs do not get equal shares of HBM bandwidth, so a fixed
+  // split of the columns leaves the pass waiting for the slowest CTAs.  When
+  // the partial rows fit in about 1% of the residual's traffic, groups take
+  // three tiers of units (60/30/10% of the columns) from a counter; otherwise
+  // each group takes one contiguous range and partials are summed per CTA.
+  const int64_t TG = (int64_t)plan->grid * plan->NG;
+  const double part_frac = 3.0 * (double)TG * 4.0 / (2.0 * (double)N * elem);
+  bool dyn = N >= 8 * TG && part_frac <= 0.01;
+  if (max_units > 0 && 3 * TG + 2 > max_units) dyn = false;
+  Units U{};
+  if (dyn) {
+    U.tg = TG;
+    U.c0 = std::max<int64_t>(1, (int64_t)(0.6 * (double)N / (double)TG));
+    U.n0 = std::min<int64_t>(N, U.c0 * TG);
+    U.c1 = std::max<int64_t>(1, (int64_t)(0.3 * (double)N / (double)TG));
+    U.n1 = std::min<int64_t>(N, U.n0 + U.c1 * TG);
+    U.c2 = std::max<int64_t>(1, (N - U.n1 + TG - 1) / TG);
+    plan->nunits = (int)(2 * TG + (N - U.n1 + U.c2 - 1) / U.c2);
+    plan->npart = plan->nunits;
+  } else {
+    U.tg = TG;
+    U.c0 = (N + TG - 1) / TG;
+    U.n0 = N;
+    U.n1 = N;
+    U.c1 = U.c2 = 1;
+    plan->nunits = (int)TG;
+    plan->npart = plan->grid;
+  }
+  plan->units = U;
+  plan->dynamic = dyn ? 1 : 0;
   return DID_OK;
 }
 
@@ -440,6 +728,7 @@ constexpr size_t kStaticScratchBytes = (size_t)6 << 20;   // 6 MiB per device
 constexpr int kStaticMaxLd = 8192;                          // rows (ld) limit
 constexpr int kStaticMaxGrid = 160;                         // CTAs limit
 constexpr int kStaticMaxSweeps = 1024;                      // sweeps per call
+constexpr int kStaticMaxUnits = 2560;                       // column units per pass
 constexpr int kStaticMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
@@ -460,9 +749,9 @@ StaticLayout static_layout() {
   L.ctrl = o;  o = align256(o + sizeof(Ctrl));
   L.degen = o; o = align256(o + sizeof(unsigned long long));
   L.trace = o; o = align256(o + sizeof(double) * kStaticMaxSweeps);
-  L.ccp = o;   o = align256(o + sizeof(double) * kStaticMaxGrid);
+  L.ccp = o;   o = align256(o + sizeof(double) * kStaticMaxUnits);
   L.sp = o;    o = align256(o + sizeof(double) * 2 * kStaticMaxGrid);
-  L.objp = o;  o = align256(o + sizeof(double) * kStaticMaxGrid);
+  L.objp = o;  o = align256(o + sizeof(double) * kStaticMaxUnits);
   L.bold = o;  o = align256(o + sizeof(float) * kStaticMaxLd);
   L.p = o;     o = align256(o + sizeof(float) * (size_t)kStaticMaxGrid * kStaticMaxLd);
   L.end = o;
@@ -507,7 +796,9 @@ extern "C" did_status did_sweep_static(float* R, int64_t ld, float* B, float* C,
   if (st != DID_OK) return st;
   SweepPlan plan{};
   char err[256];
-  st = plan_sweep((int)ld, false, kStaticMaxGrid, &plan, err, sizeof(err));
+  const int64_t unit_cap = std::min<int64_t>(kStaticMaxUnits, (int64_t)kStaticMaxGrid * kStaticMaxLd / ld);
+  // (partials are per CTA, at most kStaticMaxGrid rows, whenever units are static)
+  st = plan_sweep((int)ld, N, false, kStaticMaxGrid, unit_cap, &plan, err, sizeof(err));
   if (st != DID_OK) return st;
   if (plan.grid > kStaticMaxGrid) return DID_E_TOO_LARGE;
   cudaStream_t s = (cudaStream_t)stream;
@@ -530,6 +821,11 @@ extern "C" did_status did_sweep_static(float* R, int64_t ld, float* B, float* C,
   a.K = K;
   a.GS = plan.GS;
   a.NG = plan.NG;
+  a.D = plan.D;
+  a.units = plan.units;
+  a.nunits = plan.nunits;
+  a.dynamic = plan.dynamic;
+  a.npart = plan.npart;
   a.n_sweeps = n_sweeps;
   a.prologue = 1;       // the partials of R c_1^T are always re-formed from R
   a.stop_rule = 0;
