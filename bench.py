@@ -273,11 +273,11 @@ def main():
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     step_ms = []
-    last = info0["sweep_kernel_ms"] + info0["dense_kernel_ms"]
+    last = info0["sweep_kernel_ms"] + info0["dense_kernel_ms"] + info0["tc_refresh_ms"]
     for _ in range(args.steps):
         ctx.sweep(1)
         cur = ctx.info()
-        now = cur["sweep_kernel_ms"] + cur["dense_kernel_ms"]
+        now = cur["sweep_kernel_ms"] + cur["dense_kernel_ms"] + cur["tc_refresh_ms"]
         step_ms.append(round(now - last, 3))
         last = now
     ev1.record(stream)
@@ -309,7 +309,17 @@ def main():
     peak, peak_kind = measured_peaks()
     traffic = profiled_traffic(args.workload, args.precision)
     dense_launches = info1["dense_launches"] - info0["dense_launches"]
-    gpu_launches = launches + dense_launches
+    tc_launches = info1["tc_refreshes"] - info0["tc_refreshes"]
+    # each tensor-core refresh is three launches: two operand splits and the GEMM
+    gpu_launches = launches + dense_launches + 3 * tc_launches
+    refresh = None
+    nref = dense_launches + tc_launches
+    if nref:
+        rms = (info1["dense_kernel_ms"] - info0["dense_kernel_ms"] + info1["tc_refresh_ms"] - info0["tc_refresh_ms"]) / nref
+        rbytes = M * N * (4 + s_bytes)
+        refresh = {"kind": "tcgen05 BF16x3" if tc_launches else "SIMT FP32", "launches": int(nref),
+                   "ms_per_refresh": rms, "alg_bytes": rbytes, "GBps": rbytes / (rms / 1e3) / 1e9,
+                   "tflops": 2.0 * M * N * K * (3 if tc_launches else 1) / (rms / 1e3) / 1e12}
     ctx.close()
     del ctx
 
@@ -364,6 +374,7 @@ def main():
             "e2e": e2e,
             "gpu_launches": int(gpu_launches),
             "step_kernel_ms": step_ms,
+            "refresh": refresh,
             "phases": phases,
             "cpu_baseline": cpu,
             "clocks": clk,

@@ -85,6 +85,9 @@ typedef struct {
  * the c-pass and the end of the second grid wait.  Read with
  * did_get_phase_times; costs four 8-byte stores per k. */
 #define DID_FLAG_PHASE_TIMES 1
+/* did_options.flags: refresh a bfloat16 residual with the float32 SIMT pass
+ * instead of the tensor-core BF16x3 pass (for comparisons). */
+#define DID_FLAG_SIMT_REFRESH 2
 
 typedef struct {
     int64_t M, N;
@@ -107,6 +110,8 @@ typedef struct {
     double sweep_kernel_ms;  /* total device time of those launches */
     int64_t dense_launches;  /* refresh / objective / scaling passes */
     double dense_kernel_ms;
+    int64_t tc_refreshes;    /* refreshes done on the tensor cores */
+    double tc_refresh_ms;    /* their device time (operand split + GEMM) */
 } did_info;
 
 /* Fill *opt with the defaults: FP32, interleaved order, no refresh,
@@ -169,7 +174,10 @@ did_status did_objective(did_ctx* ctx, double* obj);
 /* 1/2 ||R||_F^2 of the stored residual (the last trace value). */
 did_status did_residual_objective(did_ctx* ctx, double* obj);
 
-/* Recompute R = X - B C densely (Algorithm 3 recomputes e_j := x_j - B c_j). */
+/* Recompute R = X - B C densely (Algorithm 3 recomputes e_j := x_j - B c_j).
+ * FP32 residual: float32 SIMT pass.  BF16 residual with K <= 128: tensor-core
+ * pass (tcgen05, three bfloat16 products Bh Ch + Bh Cl + Bl Ch with float32
+ * accumulation); larger K or DID_FLAG_SIMT_REFRESH: the SIMT pass. */
 did_status did_refresh_residual(did_ctx* ctx);
 
 /* Copy B (M x K column-major) and C (K x N row-major) out; either pointer

@@ -29,6 +29,7 @@ DID_FP32, DID_BF16R = 0, 1
 DID_ORDER_INTERLEAVED, DID_ORDER_DID = 0, 1
 DID_STOP_RELCHANGE, DID_STOP_PAPER_EPS = 0, 1
 DID_FLAG_PHASE_TIMES = 1
+DID_FLAG_SIMT_REFRESH = 2
 
 
 class did_options(ctypes.Structure):
@@ -59,7 +60,8 @@ class did_info(ctypes.Structure):
         ("refreshes", ctypes.c_int64), ("device_bytes", ctypes.c_size_t),
         ("sweep_launches", ctypes.c_int64), ("prologue_launches", ctypes.c_int64),
         ("sweep_kernel_ms", ctypes.c_double), ("dense_launches", ctypes.c_int64),
-        ("dense_kernel_ms", ctypes.c_double),
+        ("dense_kernel_ms", ctypes.c_double), ("tc_refreshes", ctypes.c_int64),
+        ("tc_refresh_ms", ctypes.c_double),
     ]
 
 

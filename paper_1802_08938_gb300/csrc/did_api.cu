@@ -41,6 +41,11 @@ struct did_ctx {
   unsigned long long* degen = nullptr;
   double* dense_part = nullptr;
   unsigned long long* bad = nullptr;
+  void* tc_ws = nullptr;            // tensor-core refresh operands (allocated on first use)
+  double* tc_part = nullptr;        // per-CTA sums of the tensor-core refresh
+  int* tc_err = nullptr;
+  int64_t tc_refreshes = 0;
+  double tc_ms = 0.0;
   uint64_t* tstamp = nullptr;       // phase stamps (DID_FLAG_PHASE_TIMES)
   int tstamp_cap = 0;
   int tstamp_n = 0;
@@ -171,10 +176,59 @@ did_status dense(did_ctx* c, int mode, double sums[3]) {
   return DID_OK;
 }
 
+// Tensor-core refresh of a bfloat16 residual; returns 1/2 ||R||^2 in *f.
+did_status refresh_tc(did_ctx* c, double* f) {
+  void* p;
+  did_status st;
+  const int G = did::refresh_tc_grid();
+  if (!c->tc_ws) {
+    st = dev_alloc(c, &p, did::refresh_tc_workspace_bytes((int)c->M, c->ld, c->N, c->K));
+    if (st != DID_OK) return st;
+    c->tc_ws = p;
+    st = dev_alloc(c, &p, sizeof(double) * G);
+    if (st != DID_OK) return st;
+    c->tc_part = (double*)p;
+    st = dev_alloc(c, &p, sizeof(int) * 4);
+    if (st != DID_OK) return st;
+    c->tc_err = (int*)p;
+  }
+  std::vector<double> part(G);
+  int herr = 0;
+  DID_CUDA(c, cudaMemsetAsync(c->tc_err, 0, sizeof(int), c->stream));
+  DID_CUDA(c, cudaEventRecord(c->ev0, c->stream));
+  DID_CUDA(c, did::launch_refresh_tc(c->X, c->R, c->B, c->C, (int)c->M, c->ld, c->N, c->K, c->tc_ws, c->tc_part,
+                                     c->tc_err, c->opt.timeout_ns ? c->opt.timeout_ns : kDefaultTimeoutNs,
+                                     c->stream));
+  DID_CUDA(c, cudaEventRecord(c->ev1, c->stream));
+  DID_CUDA(c, cudaMemcpyAsync(part.data(), c->tc_part, sizeof(double) * G, cudaMemcpyDeviceToHost, c->stream));
+  DID_CUDA(c, cudaMemcpyAsync(&herr, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  DID_CUDA(c, cudaStreamSynchronize(c->stream));
+  float ms = 0.f;
+  DID_CUDA(c, cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+  c->tc_ms += ms;
+  c->tc_refreshes++;
+  if (herr != 0) {
+    c->need_refresh = true;
+    return fail(c, DID_ETIMEOUT, "tensor-core refresh: a bounded wait ran out (device error %d)", herr);
+  }
+  double sum = 0.0;
+  for (int i = 0; i < G; ++i) sum += part[i];
+  *f = 0.5 * sum;
+  return DID_OK;
+}
+
 did_status refresh(did_ctx* c) {
   double s[3];
-  did_status st = dense(c, 0, s);
-  if (st != DID_OK) return st;
+  did_status st;
+  if (c->bf16 && did::refresh_tc_supported(c->K) && !(c->opt.flags & DID_FLAG_SIMT_REFRESH)) {
+    double f = 0.0;
+    st = refresh_tc(c, &f);
+    if (st != DID_OK) return st;
+    s[0] = 2.0 * f;
+  } else {
+    st = dense(c, 0, s);
+    if (st != DID_OK) return st;
+  }
   c->last_obj = 0.5 * s[0];
   c->need_prologue = true;
   c->need_refresh = false;
@@ -427,7 +481,7 @@ did_status did_create_ex(const float* X, int64_t M, int64_t N, int32_t K, uint64
   if (opt) o = *opt; else did_default_options(&o);
   if ((o.precision != DID_FP32 && o.precision != DID_BF16R) || (o.order != DID_ORDER_INTERLEAVED) ||
       (o.stop != DID_STOP_RELCHANGE && o.stop != DID_STOP_PAPER_EPS) || o.refresh_every < 0 ||
-      o.debug_barrier_extra < 0 || (o.flags & ~DID_FLAG_PHASE_TIMES))
+      o.debug_barrier_extra < 0 || (o.flags & ~(DID_FLAG_PHASE_TIMES | DID_FLAG_SIMT_REFRESH)))
     return DID_EINVAL;
   did_ctx* c = new did_ctx();
   c->M = M;
@@ -579,6 +633,8 @@ did_status did_get_info(did_ctx* c, did_info* info) {
   info->sweep_kernel_ms = c->sweep_ms;
   info->dense_launches = c->dense_launches;
   info->dense_kernel_ms = c->dense_ms;
+  info->tc_refreshes = c->tc_refreshes;
+  info->tc_refresh_ms = c->tc_ms;
   return DID_OK;
 }
 

@@ -336,6 +336,13 @@ struct DenseArgs {
 int dense_grid();
 cudaError_t launch_dense(const DenseArgs& a, cudaStream_t s);
 
+// Tensor-core refresh (bfloat16 residual): R = X - B C with BF16x3 products.
+bool refresh_tc_supported(int K);
+size_t refresh_tc_workspace_bytes(int M, int ld, int64_t N, int K);
+int refresh_tc_grid();
+cudaError_t launch_refresh_tc(const float* X, void* R, const float* B, const float* C, int M, int ld, int64_t N,
+                              int K, void* workspace, double* part, int* err, uint64_t timeout_ns, cudaStream_t s);
+
 // Generators.
 cudaError_t launch_gen_uniform_padded(float* out, int rows, int ld, int cols, uint64_t seed,
                                       int stream_id, cudaStream_t s);  // out[c*ld + r] = word c*rows + r

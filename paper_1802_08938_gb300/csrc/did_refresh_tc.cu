@@ -1,0 +1,417 @@
+// Dense refresh R = X - B C on the 5th-generation tensor cores (tcgen05),
+// for the bfloat16-residual mode.
+//
+// Algorithm 3 recomputes the residual e_j := x_j - B c_j at the top of every
+// iteration; the sweep keeps R and updates it in place, so a periodic dense
+// refresh resets the drift of the bfloat16 roundings.  The product B C is a
+// rank-K contraction with K <= 128, done as three bfloat16 products with
+// float32 accumulation ("BF16x3"): with B = Bh + Bl and C = Ch + Cl split into
+// bfloat16 high and low parts, B C ~= Bh Ch + Bh Cl + Bl Ch (the dropped Bl Cl
+// term is ~2^-16 relative), far below the bfloat16 rounding of the stored R.
+//
+// Kernel structure (one CTA per SM, persistent over 64-column tiles):
+//   warp 0      producer: TMA bulk copies of the C-factor tile (once per
+//               column tile), the B-factor row block (from L2) and the X tile
+//               (64 column segments of 128 rows, double buffered);
+//   warp 1      allocates 128 TMEM columns (two 128 x 64 float32 accumulators)
+//               and one elected thread issues the tcgen05.mma instructions;
+//   warps 4-7   epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
+//               lanes 32(w-4)..), R = X - D rounded to bfloat16, stored, and
+//               the sum of R^2 accumulated in float64.
+// Operands live in global memory pre-split and pre-tiled in the no-swizzle
+// K-major core-matrix layout (8 rows x 16 bytes per core matrix, core matrices
+// along K 128 bytes apart, along M/N Kp*16 bytes apart), so each operand tile
+// is one contiguous bulk copy and its shared-memory descriptor is a plain
+// (start, LBO = 128, SBO = Kp*16) triple.
+//
+// Every mbarrier wait is bounded; on expiry the kernel records the error,
+// stops issuing work, waits (bounded) for its copies and MMAs, frees its
+// TMEM and returns.
+#include "did_internal.cuh"
+
+#include <stdio.h>
+
+namespace did {
+
+namespace {
+
+constexpr int kTcThreads = 256;     // 8 warps
+constexpr int kTileM = 128;         // rows per MMA (TMEM lanes)
+constexpr int kTileN = 64;          // columns per tile (MMA N)
+constexpr int kMaxKp = 128;         // K padded to a multiple of 16, at most 128
+constexpr int kTmemCols = 128;      // two accumulators of kTileN columns
+
+struct TcArgs {
+  const float* X;            // ld x N float32, column-major
+  __nv_bfloat16* R;          // ld x N bfloat16 output
+  const __nv_bfloat16* Ahl;  // [row blocks][2][128 rows x Kp] tiled B factor (hi, lo)
+  const __nv_bfloat16* Bhl;  // [col tiles][2][64 cols x Kp] tiled C factor (hi, lo)
+  double* part;              // [grid] sum of R^2 per CTA
+  int* err;                  // error word
+  int M, ld, Kp;
+  int64_t N;
+  int row_blocks;            // ceil(ld / 128)
+  int64_t col_tiles;         // ceil(N / 64)
+  uint64_t timeout_ns;
+};
+
+// ------------------------------------------------------------- descriptors
+// Shared-memory matrix descriptor of tcgen05 (no swizzle, K-major):
+// start address >> 4 in bits 0-13, leading (K-direction) byte offset >> 4 in
+// bits 16-29, stride (M/N-direction) byte offset >> 4 in bits 32-45, the
+// descriptor version 1 in bits 46-47, base offset 0, swizzle mode 0.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// Instruction descriptor of tcgen05.mma kind::f16: dense, D float32 (bits
+// 4-5 = 1), A and B bfloat16 (bits 7-9 = 1, bits 10-12 = 1), both K-major
+// (bits 15, 16 = 0), N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+__host__ __device__ constexpr uint32_t instr_desc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// -------------------------------------------------------------- tcgen05 ops
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 16 consecutive float32 accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Bounded wait used by every role; returns false once the error word is set.
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, int* err, uint64_t timeout_ns) {
+  if (ld_volatile(err) != 0) return false;
+  return mbar_wait_bounded(bar, parity, err, timeout_ns);
+}
+
+// Shared memory plan (bytes).
+struct TcSmem {
+  size_t A, B, X, bars, tmem_slot, red, steps, total;
+};
+__host__ __device__ __forceinline__ TcSmem tc_smem(int Kp) {
+  TcSmem L;
+  size_t o = 0;
+  L.A = o;    o += (size_t)2 * kTileM * Kp * 2;          // Bh, Bl row block
+  L.B = o;    o += (size_t)2 * kTileN * Kp * 2;          // Ch, Cl column tile
+  L.X = o;    o += (size_t)2 * kTileN * kTileM * 4;      // two X tiles [64 cols][128 rows]
+  L.bars = o; o += 16 * sizeof(uint64_t);
+  L.tmem_slot = o; o += 16;
+  L.red = o;  o += 8 * sizeof(double);
+  L.steps = o; o += 16;
+  L.total = o;
+  return L;
+}
+
+// Barrier slots.
+enum {
+  BAR_B_FULL = 0,     // C-factor tile landed
+  BAR_A_FULL = 1,     // B-factor row block landed
+  BAR_A_EMPTY = 2,    // MMAs of the row block done reading A (and B)
+  BAR_X_FULL = 3,     // 3, 4: X tile buffers landed
+  BAR_X_EMPTY = 5,    // 5, 6: epilogue done with an X buffer (count 4 warps)
+  BAR_ACC_FULL = 7,   // 7, 8: accumulator ready (tcgen05.commit)
+  BAR_ACC_EMPTY = 9,  // 9, 10: epilogue done reading an accumulator (count 4 warps)
+  BAR_COUNT = 11
+};
+
+__global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  const TcSmem L = tc_smem(a.Kp);
+  unsigned char* sA = sm + L.A;
+  unsigned char* sB = sm + L.B;
+  float* sX = reinterpret_cast<float*>(sm + L.X);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + L.bars);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + L.tmem_slot);
+  double* red = reinterpret_cast<double*>(sm + L.red);
+  int* mma_steps = reinterpret_cast<int*>(sm + L.steps);   // steps whose MMAs were committed
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int Kp = a.Kp;
+  const uint32_t a_bytes = 2u * kTileM * Kp * 2;
+  const uint32_t b_bytes = 2u * kTileN * Kp * 2;
+  const uint32_t a_split = (uint32_t)kTileM * Kp * 2;     // bytes of one split of the A tile
+  const uint32_t b_split = (uint32_t)kTileN * Kp * 2;
+
+  if (threadIdx.x == 0) {
+    *mma_steps = 0;
+    for (int i = 0; i < BAR_COUNT; ++i) {
+      const bool per_warp = (i == BAR_X_EMPTY || i == BAR_X_EMPTY + 1 || i == BAR_ACC_EMPTY || i == BAR_ACC_EMPTY + 1);
+      mbar_init(bars + i, per_warp ? 4 : 1);
+    }
+  }
+  fence_mbar_init();
+  if (warp == 1) tmem_alloc(tmem_slot, kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  // The CTA's work list: column tiles t = blockIdx.x + i*grid, each with all
+  // row blocks.  Step s enumerates (tile, row block) pairs in that order.
+  const int64_t ntile_cta = a.col_tiles > blockIdx.x ? (a.col_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t nsteps = ntile_cta * a.row_blocks;
+  int* err = a.err;
+  const uint64_t tmo = a.timeout_ns;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      for (int64_t s = 0; s < nsteps; ++s) {
+        const int64_t ti = s / a.row_blocks;
+        const int rb = (int)(s % a.row_blocks);
+        const int64_t tile = blockIdx.x + ti * gridDim.x;
+        const int64_t j0 = tile * kTileN;
+        if (rb == 0) {
+          // previous tile's MMAs must be done with the C-factor buffer
+          if (s > 0 && !tc_wait(bars + BAR_A_EMPTY, (uint32_t)((s - 1) & 1), err, tmo)) break;
+          mbar_arrive_expect_tx(bars + BAR_B_FULL, b_bytes);
+          bulk_load(sB, reinterpret_cast<const unsigned char*>(a.Bhl) + (size_t)tile * b_bytes, b_bytes,
+                    bars + BAR_B_FULL);
+        } else {
+          if (!tc_wait(bars + BAR_A_EMPTY, (uint32_t)((s - 1) & 1), err, tmo)) break;
+        }
+        mbar_arrive_expect_tx(bars + BAR_A_FULL, a_bytes);
+        bulk_load(sA, reinterpret_cast<const unsigned char*>(a.Ahl) + (size_t)rb * a_bytes, a_bytes,
+                  bars + BAR_A_FULL);
+        // X tile: 64 column segments of up to 128 rows into buffer s & 1
+        const int xb = (int)(s & 1);
+        if (s >= 2 && !tc_wait(bars + BAR_X_EMPTY + xb, (uint32_t)(((s - 2) >> 1) & 1), err, tmo)) break;
+        const int i0 = rb * kTileM;
+        const int rows = a.ld - i0 < kTileM ? a.ld - i0 : kTileM;
+        const int ncol = a.N - j0 < kTileN ? (int)(a.N - j0) : kTileN;
+        mbar_arrive_expect_tx(bars + BAR_X_FULL + xb, (uint32_t)(rows * 4 * ncol));
+        float* xdst = sX + (size_t)xb * kTileN * kTileM;
+        for (int c = 0; c < ncol; ++c)
+          bulk_load(xdst + c * kTileM, a.X + (size_t)(j0 + c) * a.ld + i0, (uint32_t)(rows * 4),
+                    bars + BAR_X_FULL + xb);
+      }
+    }
+  } else if (warp == 1) {
+    // ----------------------------------------------------------- MMA issue
+    if (lane == 0) {
+      const uint32_t idesc = instr_desc_bf16(kTileM, kTileN);
+      const uint32_t sA0 = smem_u32(sA), sB0 = smem_u32(sB);
+      const uint32_t sbo = (uint32_t)Kp * 16;   // next 8-row group
+      for (int64_t s = 0; s < nsteps; ++s) {
+        const int rb = (int)(s % a.row_blocks);
+        const int64_t ti = s / a.row_blocks;
+        if (rb == 0 && !tc_wait(bars + BAR_B_FULL, (uint32_t)(ti & 1), err, tmo)) break;
+        if (!tc_wait(bars + BAR_A_FULL, (uint32_t)(s & 1), err, tmo)) break;
+        const int ab = (int)(s & 1);
+        if (s >= 2 && !tc_wait(bars + BAR_ACC_EMPTY + ab, (uint32_t)(((s - 2) >> 1) & 1), err, tmo)) break;
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(ab * kTileN);
+        uint32_t acc = 0;
+        // Bh Ch, Bh Cl, Bl Ch
+        for (int prod = 0; prod < 3; ++prod) {
+          const uint32_t aoff = prod == 2 ? a_split : 0u;
+          const uint32_t boff = prod == 1 ? b_split : 0u;
+          for (int kk = 0; kk < Kp / 16; ++kk) {
+            const uint64_t ad = smem_desc(sA0 + aoff + (uint32_t)kk * 256u, 128u, sbo);
+            const uint64_t bd = smem_desc(sB0 + boff + (uint32_t)kk * 256u, 128u, sbo);
+            mma_bf16(d, ad, bd, idesc, acc);
+            acc = 1;
+          }
+        }
+        mma_commit(bars + BAR_ACC_FULL + ab);
+        mma_commit(bars + BAR_A_EMPTY);
+        *mma_steps = (int)(s + 1);
+      }
+    }
+  } else if (warp >= 4) {
+    // ------------------------------------------------------------- epilogue
+    const int ew = warp - 4;                 // TMEM lane quarter
+    const int row_in = ew * 32 + lane;
+    double acc2 = 0.0;
+    bool ok = true;
+    for (int64_t s = 0; s < nsteps && ok; ++s) {
+      const int64_t ti = s / a.row_blocks;
+      const int rb = (int)(s % a.row_blocks);
+      const int64_t tile = blockIdx.x + ti * gridDim.x;
+      const int64_t j0 = tile * kTileN;
+      const int ab = (int)(s & 1), xb = (int)(s & 1);
+      ok = tc_wait(bars + BAR_ACC_FULL + ab, (uint32_t)((s >> 1) & 1), err, tmo) &&
+           tc_wait(bars + BAR_X_FULL + xb, (uint32_t)((s >> 1) & 1), err, tmo);
+      tc_fence_after();
+      float d[kTileN];
+#pragma unroll
+      for (int c = 0; c < kTileN; c += 16)
+        tmem_ld16(tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(ab * kTileN + c), d + c);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bars + BAR_ACC_EMPTY + ab);
+      const int i = rb * kTileM + row_in;
+      const float* xs = sX + (size_t)xb * kTileN * kTileM + row_in;
+      const int ncol = a.N - j0 < kTileN ? (int)(a.N - j0) : kTileN;
+      float s2 = 0.f;
+      if (ok && i < a.ld) {
+        __nv_bfloat16* rp = a.R + (size_t)j0 * a.ld + i;
+#pragma unroll
+        for (int c = 0; c < kTileN; ++c) {
+          if (c < ncol) {
+            const float r = xs[c * kTileM] - d[c];
+            const __nv_bfloat16 rb16 = __float2bfloat16_rn(r);
+            rp[(size_t)c * a.ld] = rb16;
+            const float rr = __bfloat162float(rb16);
+            s2 = fmaf(rr, rr, s2);
+          }
+        }
+      }
+      acc2 += (double)s2;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bars + BAR_X_EMPTY + xb);
+    }
+    // CTA partial of sum R^2 over the 4 epilogue warps, in warp order.
+    acc2 = warp_sum_f64(acc2);
+    if (lane == 0) red[ew] = acc2;
+  }
+
+  // Drain: every issued MMA must finish before TMEM is freed.  The last
+  // commit of the MMA thread arrives on BAR_A_EMPTY; its phase is waited here
+  // (bounded) by warp 1, then the allocation is released.
+  __syncthreads();
+  const int issued = *mma_steps;
+  if (warp == 1 && lane == 0 && issued > 0) {
+    mbar_wait_bounded(bars + BAR_A_EMPTY, (uint32_t)((issued - 1) & 1), err, tmo);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem, kTmemCols);
+  if (threadIdx.x == 0) a.part[blockIdx.x] = red[0] + red[1] + red[2] + red[3];
+}
+
+// ------------------------------------------------------------ operand prep
+// Tiled no-swizzle K-major layout of one split of a tile of `rows` rows:
+// element (r, k) at byte ((r/8) * (Kp/8) + k/8) * 128 + (r%8) * 16 + (k%8) * 2.
+__device__ __forceinline__ size_t tiled_index(int r, int k, int Kp) {
+  return ((size_t)(r >> 3) * (Kp >> 3) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7);   // in elements
+}
+
+// B factor (ld x K column-major float32) -> [row block][split][128 x Kp].
+__global__ void prep_b_kernel(const float* B, int M, int ld, int K, int Kp, int row_blocks, __nv_bfloat16* out) {
+  const int64_t n = (int64_t)row_blocks * kTileM * Kp;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(idx % Kp);
+    const int64_t rg = idx / Kp;                 // global row
+    const int rb = (int)(rg / kTileM), r = (int)(rg % kTileM);
+    const float v = (rg < M && k < K) ? B[(size_t)k * ld + rg] : 0.f;
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+    __nv_bfloat16* base = out + (size_t)rb * 2 * kTileM * Kp;
+    base[tiled_index(r, k, Kp)] = hi;
+    base[(size_t)kTileM * Kp + tiled_index(r, k, Kp)] = lo;
+  }
+}
+
+// C factor (K x N row-major float32) -> [column tile][split][64 x Kp].
+__global__ void prep_c_kernel(const float* C, int64_t N, int K, int Kp, int64_t col_tiles, __nv_bfloat16* out) {
+  const int64_t n = col_tiles * kTileN * Kp;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(idx % Kp);
+    const int64_t cg = idx / Kp;                 // global column
+    const int64_t ct = cg / kTileN;
+    const int c = (int)(cg % kTileN);
+    const float v = (cg < N && k < K) ? C[(size_t)k * N + cg] : 0.f;
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+    __nv_bfloat16* base = out + (size_t)ct * 2 * kTileN * Kp;
+    base[tiled_index(c, k, Kp)] = hi;
+    base[(size_t)kTileN * Kp + tiled_index(c, k, Kp)] = lo;
+  }
+}
+
+int sm_count_tc() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
+}
+
+}  // namespace
+
+bool refresh_tc_supported(int K) { return K >= 1 && K <= kMaxKp; }
+
+size_t refresh_tc_workspace_bytes(int M, int ld, int64_t N, int K) {
+  const int Kp = (K + 15) / 16 * 16;
+  const int row_blocks = (ld + kTileM - 1) / kTileM;
+  const int64_t col_tiles = (N + kTileN - 1) / kTileN;
+  (void)M;
+  return (size_t)row_blocks * 2 * kTileM * Kp * 2 + (size_t)col_tiles * 2 * kTileN * Kp * 2;
+}
+
+int refresh_tc_grid() { return sm_count_tc(); }
+
+cudaError_t launch_refresh_tc(const float* X, void* R, const float* B, const float* C, int M, int ld, int64_t N, int K,
+                              void* workspace, double* part, int* err, uint64_t timeout_ns, cudaStream_t s) {
+  const int Kp = (K + 15) / 16 * 16;
+  const int row_blocks = (ld + kTileM - 1) / kTileM;
+  const int64_t col_tiles = (N + kTileN - 1) / kTileN;
+  __nv_bfloat16* Ahl = static_cast<__nv_bfloat16*>(workspace);
+  __nv_bfloat16* Bhl = Ahl + (size_t)row_blocks * 2 * kTileM * Kp;
+  const int sms = sm_count_tc();
+  prep_b_kernel<<<sms * 4, 256, 0, s>>>(B, M, ld, K, Kp, row_blocks, Ahl);
+  prep_c_kernel<<<sms * 8, 256, 0, s>>>(C, N, K, Kp, col_tiles, Bhl);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  TcArgs a{};
+  a.X = X;
+  a.R = static_cast<__nv_bfloat16*>(R);
+  a.Ahl = Ahl;
+  a.Bhl = Bhl;
+  a.part = part;
+  a.err = err;
+  a.M = M;
+  a.ld = ld;
+  a.Kp = Kp;
+  a.N = N;
+  a.row_blocks = row_blocks;
+  a.col_tiles = col_tiles;
+  a.timeout_ns = timeout_ns;
+  const size_t smem = tc_smem(Kp).total;
+  e = cudaFuncSetAttribute(refresh_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  refresh_tc_kernel<<<sms, kTcThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace did
