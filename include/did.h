@@ -232,6 +232,72 @@ did_status did_generate_image(float* X_dev, int64_t M, int64_t N, uint64_t seed,
 did_status did_generate_uniform(float* out_dev, int64_t n, uint64_t seed, int32_t stream_id,
                                 void* stream);
 
+/* ------------------------------------------------------------------------
+ * Serving: a queue of factorisation requests of different M, N, K solved
+ * concurrently on one GPU (continuous batching).
+ *
+ * A server owns a worker thread.  Submitted requests wait in a FIFO queue;
+ * one is admitted when a slot is free and its device memory (X, R, B, C and
+ * partials: about M*N*(4 + s) bytes, s = 4 FP32 or 2 BF16-R) fits in the HBM
+ * budget.  Admitted requests keep X, R, B and C resident on the device.  The
+ * worker runs rounds: one cooperative launch of the multi-instance sweep
+ * kernel runs up to `round_sweeps` sweeps of every active request, each on
+ * its own range of CTAs (sized by its work) with its own grid barriers and
+ * stopping test (|f_{t-1} - f_t| / f_{t-1} < tol, or max_iter sweeps).
+ * Between rounds, finished requests are retired (B, C copied to host memory
+ * owned by the server, device memory freed) and waiting ones admitted, so
+ * requests arriving while others run join at the next round.  The start
+ * point is the seeded one of did_create; the order is interleaved.
+ * All times are seconds on a steady host clock, from server creation.
+ * ---------------------------------------------------------------------- */
+typedef struct did_server did_server;
+
+typedef struct {
+    const float* X;      /* host or device, M x N column-major; NULL: generate
+                            X = B0 C0 + 0.01 |N(0,1)| with B0, C0 ~ U[0,1) from seed */
+    int64_t M, N;
+    int32_t K;
+    uint64_t seed;
+    int32_t max_iter;    /* sweep limit */
+    double tol;          /* relative-change tolerance (0: run max_iter sweeps) */
+} did_request;
+
+typedef struct {
+    did_status status;   /* DID_PENDING until done */
+    int32_t iters;       /* sweeps run */
+    double obj;          /* last 1/2 ||R||^2 */
+    double t_submit, t_start, t_done;
+} did_result;
+
+typedef struct {
+    int64_t submitted, completed, failed;
+    double solves_per_s;     /* completed / (last completion - first submission) */
+    double p50_ms, p99_ms;   /* latency t_done - t_submit of completed requests */
+    size_t peak_bytes;       /* largest device memory held for requests at once */
+    int32_t peak_active;     /* largest number of requests in one round */
+    int64_t rounds;
+    double busy_s;           /* device time of the rounds (CUDA events) */
+} did_server_stats_t;
+
+/* max_slots: requests active at once (<= CTAs of one launch); round_sweeps:
+ * sweeps per round (1..64; smaller admits sooner); stream: NULL = the server
+ * creates its own. */
+did_status did_server_create(size_t hbm_budget_bytes, did_precision precision, int32_t max_slots,
+                             int32_t round_sweeps, void* stream, did_server** out);
+/* Queue a request (copied); *ticket identifies it.  DID_E_TOO_LARGE if it can
+ * never fit (M beyond the kernel's limit or its memory above the budget). */
+did_status did_server_submit(did_server* srv, const did_request* req, uint64_t* ticket);
+/* DID_PENDING while queued or running, else the request's final status. */
+did_status did_server_poll(did_server* srv, uint64_t ticket, did_result* res);
+/* Block until done or timeout_ms (< 0: no limit); DID_PENDING on timeout. */
+did_status did_server_wait(did_server* srv, uint64_t ticket, int32_t timeout_ms, did_result* res);
+/* Copy the finished request's B (M x K column-major) and C (K x N row-major)
+ * to host or device buffers (either may be NULL), then release them. */
+did_status did_server_fetch(did_server* srv, uint64_t ticket, float* B, float* C);
+did_status did_server_stats(did_server* srv, did_server_stats_t* stats);
+/* Finish every queued and running request, stop the worker, free all memory. */
+void did_server_destroy(did_server* srv);
+
 #ifdef __cplusplus
 }
 #endif

@@ -65,6 +65,23 @@ class did_info(ctypes.Structure):
     ]
 
 
+class did_request(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("M", ctypes.c_int64), ("N", ctypes.c_int64), ("K", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("max_iter", ctypes.c_int32), ("tol", ctypes.c_double)]
+
+
+class did_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("obj", ctypes.c_double),
+                ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+class did_server_stats_t(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("solves_per_s", ctypes.c_double), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("peak_bytes", ctypes.c_size_t), ("peak_active", ctypes.c_int32), ("rounds", ctypes.c_int64),
+                ("busy_s", ctypes.c_double)]
+
+
 class DIDError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__("%s: %s" % (status_string(status), msg))
@@ -99,6 +116,13 @@ def _load():
         "did_generate_planted": (I32, [P, I64, I64, I32, U64, I32, D, D, D, D, P]),
         "did_generate_image": (I32, [P, I64, I64, U64, D, P]),
         "did_generate_uniform": (I32, [P, I64, U64, I32, P]),
+        "did_server_create": (I32, [ctypes.c_size_t, I32, I32, I32, P, ctypes.POINTER(CTX)]),
+        "did_server_submit": (I32, [CTX, ctypes.POINTER(did_request), ctypes.POINTER(U64)]),
+        "did_server_poll": (I32, [CTX, U64, ctypes.POINTER(did_result)]),
+        "did_server_wait": (I32, [CTX, U64, I32, ctypes.POINTER(did_result)]),
+        "did_server_fetch": (I32, [CTX, U64, P, P]),
+        "did_server_stats": (I32, [CTX, ctypes.POINTER(did_server_stats_t)]),
+        "did_server_destroy": (None, [CTX]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -251,6 +275,53 @@ def did_generate_uniform(out_dev, n, seed, stream_id, stream=None):
     _check(_lib.did_generate_uniform(_ptr(out_dev), n, seed, stream_id, _stream_of(stream)))
 
 
+def did_server_create(hbm_budget_bytes, precision=DID_FP32, max_slots=64, round_sweeps=4, stream=None):
+    h = ctypes.c_void_p()
+    st = _lib.did_server_create(int(hbm_budget_bytes), precision, max_slots, round_sweeps,
+                                stream if isinstance(stream, (int, type(None))) else stream.cuda_stream,
+                                ctypes.byref(h))
+    _check(st)
+    return h
+
+
+def did_server_submit(h, M, N, K, seed, max_iter, tol, X=None):
+    r = did_request(_ptr(X), M, N, K, seed, max_iter, tol)
+    t = ctypes.c_uint64()
+    _check(_lib.did_server_submit(h, ctypes.byref(r), ctypes.byref(t)))
+    return t.value
+
+
+def _result_dict(st, r):
+    return {"status": st, "iters": r.iters, "obj": r.obj, "t_submit": r.t_submit, "t_start": r.t_start,
+            "t_done": r.t_done}
+
+
+def did_server_poll(h, ticket):
+    r = did_result()
+    st = _lib.did_server_poll(h, ticket, ctypes.byref(r))
+    return _result_dict(st, r)
+
+
+def did_server_wait(h, ticket, timeout_ms=-1):
+    r = did_result()
+    st = _lib.did_server_wait(h, ticket, timeout_ms, ctypes.byref(r))
+    return _result_dict(st, r)
+
+
+def did_server_fetch(h, ticket, B, C):
+    _check(_lib.did_server_fetch(h, ticket, _ptr(B), _ptr(C)))
+
+
+def did_server_stats(h):
+    s = did_server_stats_t()
+    _check(_lib.did_server_stats(h, ctypes.byref(s)))
+    return {k: getattr(s, k) for k, _ in did_server_stats_t._fields_}
+
+
+def did_server_destroy(h):
+    _lib.did_server_destroy(h)
+
+
 # --------------------------------------------------------------- convenience
 class Context:
     """Owns one did_ctx.  X is M x N column-major (C-contiguous (N, M))."""
@@ -313,6 +384,52 @@ class Context:
     def close(self):
         if getattr(self, "h", None):
             did_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Owns one did_server (continuous batching of factorisation requests)."""
+
+    def __init__(self, hbm_budget_bytes, precision=DID_FP32, max_slots=64, round_sweeps=4, stream=None):
+        self.h = did_server_create(hbm_budget_bytes, precision, max_slots, round_sweeps, stream)
+        self.shapes = {}
+
+    def submit(self, M, N, K, seed, max_iter=300, tol=1e-4, X=None):
+        t = did_server_submit(self.h, M, N, K, seed, max_iter, tol, X)
+        self.shapes[t] = (M, N, K)
+        return t
+
+    def poll(self, ticket):
+        return did_server_poll(self.h, ticket)
+
+    def wait(self, ticket, timeout_ms=-1):
+        return did_server_wait(self.h, ticket, timeout_ms)
+
+    def fetch(self, ticket):
+        M, N, K = self.shapes[ticket]
+        Bt = np.empty((K, M), dtype=np.float32)
+        C = np.empty((K, N), dtype=np.float32)
+        did_server_fetch(self.h, ticket, Bt, C)
+        return Bt.T, C
+
+    def stats(self):
+        return did_server_stats(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            did_server_destroy(self.h)
             self.h = None
 
     def __enter__(self):

@@ -228,6 +228,12 @@ cudaError_t launch_dense(const DenseArgs& a, cudaStream_t s) {
 cudaError_t launch_gen_planted_x(float* X, const float* B0, const float* C0, int M, int64_t N, int K,
                                  uint64_t seed, double sigma, double salt_frac, double salt_value,
                                  cudaStream_t s) {
+  return launch_gen_planted_x_ld(X, M, B0, C0, M, N, K, seed, sigma, salt_frac, salt_value, s);
+}
+
+cudaError_t launch_gen_planted_x_ld(float* X, int ldx, const float* B0, const float* C0, int M, int64_t N, int K,
+                                    uint64_t seed, double sigma, double salt_frac, double salt_value,
+                                    cudaStream_t s) {
   DenseTileArgs t{};
   t.d.X = nullptr;
   t.d.R = X;
@@ -235,7 +241,7 @@ cudaError_t launch_gen_planted_x(float* X, const float* B0, const float* C0, int
   t.d.C = C0;
   t.d.part = nullptr;
   t.d.M = M;
-  t.d.ld = M;
+  t.d.ld = ldx;
   t.d.K = K;
   t.d.N = N;
   t.d.mode = 3;

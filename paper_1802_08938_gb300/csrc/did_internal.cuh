@@ -304,6 +304,8 @@ struct SweepArgs {
   uint64_t timeout_ns;
   uint64_t* tstamp;   // optional phase stamps (CTA 0), 4 per k; nullptr = off
   int tstamp_cap;     // number of k-steps that fit in tstamp
+  int cta_begin;      // multi-instance launch: first CTA of this instance
+  int cta_count;      // multi-instance launch: CTAs of this instance
 };
 
 struct SweepPlan {
@@ -319,6 +321,13 @@ struct SweepPlan {
 did_status plan_sweep(int ld, int64_t N, bool bf16, int grid_override, int64_t max_units, SweepPlan* plan,
                       char* err, size_t errlen);
 cudaError_t launch_sweep(const SweepPlan& plan, const SweepArgs& args, cudaStream_t s);
+
+// Multi-instance sweeps (serving): one cooperative launch runs several
+// instances, each on its own range of CTAs (SweepArgs::cta_begin/cta_count).
+int serve_max_ld(bool bf16);
+did_status serve_launch_config(bool bf16, int* grid, size_t* smem_budget);
+did_status plan_instance(int ld, int64_t N, bool bf16, int ncta, size_t smem_budget, SweepPlan* plan);
+cudaError_t launch_sweep_multi(bool bf16, const SweepArgs* d_inst, int ninst, int grid, size_t smem, cudaStream_t s);
 
 // Dense pass over tiles of X - B C:
 //   mode 0: R = X - B C stored (float or bf16); sums[0] += sum R^2
@@ -353,6 +362,10 @@ cudaError_t launch_gen_planted_x(float* X, const float* B0, const float* C0, int
                                  uint64_t seed, double sigma, double salt_frac, double salt_value,
                                  cudaStream_t s);
 cudaError_t launch_gen_image(float* X, int M, int64_t N, uint64_t seed, double zero_frac, cudaStream_t s);
+// As launch_gen_planted_x with leading dimension ldx >= M (rows M..ldx-1 untouched).
+cudaError_t launch_gen_planted_x_ld(float* X, int ldx, const float* B0, const float* C0, int M, int64_t N, int K,
+                                    uint64_t seed, double sigma, double salt_frac, double salt_value,
+                                    cudaStream_t s);
 
 // Elementwise helpers.
 cudaError_t launch_check_nonneg_finite(const float* X, int rows, int ld, int64_t cols,

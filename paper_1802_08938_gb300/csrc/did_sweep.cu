@@ -115,9 +115,9 @@ struct SmemPtrs {
 // the stages this group has consumed since the launch (stage and phase).
 // Vector slots r < NR-1 are always inside the column (NR = ceil(nvec / GS));
 // only the last slot needs a bounds test.
-template <int NR, bool BF16, int MODE, bool OBJ>
-__device__ __forceinline__ void column_pass(const SweepArgs& a, int k, int knext, float inv_bb, float alpha,
-                                            bool cdeg, const SmemPtrs& sm, unsigned& it, int pass) {
+template <int NR, bool BF16, int MODE, bool OBJ, bool GEN>
+__device__ __forceinline__ void column_pass(const SweepArgs& a, int cta, int k, int knext, float inv_bb,
+                                            float alpha, bool cdeg, const SmemPtrs& sm, unsigned& it, int pass) {
   typedef Vec<BF16> V;
   typedef typename V::raw raw;
   constexpr int VR = V::kRows;
@@ -141,11 +141,15 @@ __device__ __forceinline__ void column_pass(const SweepArgs& a, int k, int knext
   uint64_t* bars = sm.mbar + g * D;
   volatile int64_t* meta = sm.meta + g * D;
   const bool last_ok = lt + (NR - 1) * GS < nvec;       // the last slot of this thread is in range
+  // Slot r of this thread holds vector q = lt + r*GS of the column.  With the
+  // planner's NR = ceil(nvec / GS) only the last slot can fall outside; GEN
+  // (instances of several shapes in one launch) tests every slot.
+  auto slot_ok = [&](int r) -> bool { return GEN ? (lt + r * GS < nvec) : (r < NR - 1 || last_ok); };
   const float* bo_base = sm.bo;
   const int half = ld / 2;
-  const int gg = blockIdx.x * a.NG + g;
+  const int gg = cta * a.NG + g;
 
-  if (blockIdx.x == 0 && threadIdx.x == 0) a.ctrl->work[(pass + 1) & 1] = 0u;   // next pass's counter
+  if (cta == 0 && threadIdx.x == 0) a.ctrl->work[(pass + 1) & 1] = 0u;   // next pass's counter
 
   // b_k' for this thread's rows: registers for an FP32 residual; for a BF16
   // residual (twice the rows per vector) it is read from shared memory.
@@ -155,7 +159,7 @@ __device__ __forceinline__ void column_pass(const SweepArgs& a, int k, int knext
 #pragma unroll
   for (int r = 0; r < NR; ++r) {
     const int q = lt + r * GS;
-    const bool ok = r < NR - 1 || last_ok;
+    const bool ok = slot_ok(r);
 #pragma unroll
     for (int e = 0; e < VR; e += 4) {
       if (!BF16) {
@@ -233,7 +237,7 @@ __device__ __forceinline__ void column_pass(const SweepArgs& a, int k, int knext
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
       const int q = lt + r * GS;
-      if (r < NR - 1 || last_ok) {
+      if (slot_ok(r)) {
 #pragma unroll
         for (int e = 0; e < VR; e += 4)
           __stcg(reinterpret_cast<float4*>(Pu + q * VR + e),
@@ -295,7 +299,7 @@ __device__ __forceinline__ void column_pass(const SweepArgs& a, int k, int knext
       float2 d2 = make_float2(0.f, 0.f);
 #pragma unroll
       for (int r = 0; r < NR; ++r) {
-        if (r < NR - 1 || last_ok) {
+        if (slot_ok(r)) {
           float f[VR];
           V::unpack(stage[r * GS], f);
 #pragma unroll
@@ -328,7 +332,7 @@ __device__ __forceinline__ void column_pass(const SweepArgs& a, int k, int knext
     float2 s2 = make_float2(0.f, 0.f);
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
-      if (r < NR - 1 || last_ok) {
+      if (slot_ok(r)) {
         const int q = lt + r * GS;
         float f[VR];
         V::unpack(stage[r * GS], f);
@@ -372,7 +376,7 @@ __device__ __forceinline__ void column_pass(const SweepArgs& a, int k, int knext
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
       const int q = lt + r * GS;
-      if (r < NR - 1 || last_ok) {
+      if (slot_ok(r)) {
 #pragma unroll
         for (int e = 0; e < VR; e += 4)
           *reinterpret_cast<float4*>(pg + (size_t)g * ld + q * VR + e) =
@@ -380,17 +384,17 @@ __device__ __forceinline__ void column_pass(const SweepArgs& a, int k, int knext
       }
     }
     __syncthreads();
-    float* Pc = a.P + (size_t)blockIdx.x * ld;
+    float* Pc = a.P + (size_t)cta * ld;
     for (int idx = threadIdx.x; idx < ld; idx += blockDim.x) {
       float sum = 0.f;
       for (int gi = 0; gi < a.NG; ++gi) sum += pg[(size_t)gi * ld + idx];
       __stcg(Pc + idx, sum);
     }
     const double cc = block_sum_f64(cc_acc, sm.dscr);
-    if (threadIdx.x == 0) __stcg(a.CCp + blockIdx.x, cc);
+    if (threadIdx.x == 0) __stcg(a.CCp + cta, cc);
     if (OBJ) {
       const double o = block_sum_f64(obj_acc, sm.dscr);
-      if (threadIdx.x == 0) __stcg(a.OBJp + blockIdx.x, o);
+      if (threadIdx.x == 0) __stcg(a.OBJp + cta, o);
     }
     __syncthreads();   // the ring is free again before the next pass primes it
   }
@@ -401,8 +405,7 @@ __device__ __forceinline__ void column_pass(const SweepArgs& a, int k, int knext
 // slice.  The slice's rows are spread over the CTA's threads together with
 // interleaved subsets of the partial rows (up to 16 loads in flight each);
 // the subsets' sums are added in subset order.
-__device__ __forceinline__ void b_reduce(const SweepArgs& a, int k, float* acc, double* bc) {
-  const int G = gridDim.x;
+__device__ __forceinline__ void b_reduce(const SweepArgs& a, int cta, int G, int k, float* acc, double* bc) {
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   const int U = a.npart;
   if (w == 0) {
@@ -410,7 +413,7 @@ __device__ __forceinline__ void b_reduce(const SweepArgs& a, int k, float* acc, 
     if (l == 0) bc[0] = cc;
   }
   const int rpc = (a.ld + G - 1) / G;
-  const int r0 = blockIdx.x * rpc;
+  const int r0 = cta * rpc;
   const int r1 = min(a.ld, r0 + rpc);
   const int nrows = max(0, r1 - r0);
   double bb = 0.0, bob = 0.0;
@@ -460,15 +463,16 @@ __device__ __forceinline__ void b_reduce(const SweepArgs& a, int k, float* acc, 
     bb = warp_sum_f64(bb);
     bob = warp_sum_f64(bob);
     if (l == 0) {
-      __stcg(a.Sp + 2 * blockIdx.x, bb);
-      __stcg(a.Sp + 2 * blockIdx.x + 1, bob);
+      __stcg(a.Sp + 2 * cta, bb);
+      __stcg(a.Sp + 2 * cta + 1, bob);
     }
   }
-  if (!(cc > 0.0) && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(a.degen, 1ull);
+  if (!(cc > 0.0) && cta == 0 && threadIdx.x == 0) atomicAdd(a.degen, 1ull);
 }
 
-template <int NR, bool BF16>
-__global__ void __launch_bounds__(kSweepThreads, 1) sweep_kernel(SweepArgs a) {
+// Whole sweeps of one instance on CTAs cta = 0..ncta-1 of its view.
+template <int NR, bool BF16, bool GEN>
+__device__ __forceinline__ void sweep_body(const SweepArgs& a, int cta, int ncta) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const SweepSmem L = sweep_smem(a.ld, a.NG, a.D, BF16 ? 2 : 4);
   SmemPtrs sm;
@@ -482,7 +486,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_kernel(SweepArgs a) {
   sm.bc = reinterpret_cast<double*>(smem_raw + L.bc);
   sm.mbar = reinterpret_cast<uint64_t*>(smem_raw + L.mbar);
   double* bc = sm.bc;
-  const int G = gridDim.x;
+  const int G = ncta;
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   unsigned nbar = 0;
   unsigned it = 0;     // stages consumed by this thread's column group
@@ -501,19 +505,19 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_kernel(SweepArgs a) {
   } while (0)
 
   if (a.prologue) {
-    column_pass<NR, BF16, kPrologue, false>(a, 0, 0, 0.f, 0.f, true, sm, it, pass++);
+    column_pass<NR, BF16, kPrologue, false, GEN>(a, cta, 0, 0, 0.f, 0.f, true, sm, it, pass++);
     DID_GRID_SYNC();
   }
   const double f0 = a.f0;
   double f_prev = a.f_prev;
 
-  const bool stamps = a.tstamp != nullptr && blockIdx.x == 0 && threadIdx.x == 0;
+  const bool stamps = a.tstamp != nullptr && cta == 0 && threadIdx.x == 0;
   for (int s = 0; s < a.n_sweeps; ++s) {
     for (int k = 0; k < a.K; ++k) {
       const int step = s * a.K + k;
       const bool rec = stamps && step < a.tstamp_cap;
       if (rec) a.tstamp[4 * step + 0] = globaltimer_ns();
-      b_reduce(a, k, sm.red, bc);
+      b_reduce(a, cta, G, k, sm.red, bc);
       DID_GRID_SYNC();
       if (rec) a.tstamp[4 * step + 1] = globaltimer_ns();
       if (w == 0) {
@@ -536,12 +540,12 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_kernel(SweepArgs a) {
       const bool cdeg = !(bb > 0.0);
       const float inv_bb = cdeg ? 0.f : (float)(1.0 / bb);
       const float alpha = cdeg ? 0.f : (float)(bob / bb);
-      if (cdeg && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(a.degen, 1ull);
+      if (cdeg && cta == 0 && threadIdx.x == 0) atomicAdd(a.degen, 1ull);
       const int knext = (k + 1 < a.K) ? k + 1 : 0;
       if (k == a.K - 1)
-        column_pass<NR, BF16, kUpdateC, true>(a, k, knext, inv_bb, alpha, cdeg, sm, it, pass++);
+        column_pass<NR, BF16, kUpdateC, true, GEN>(a, cta, k, knext, inv_bb, alpha, cdeg, sm, it, pass++);
       else
-        column_pass<NR, BF16, kUpdateC, false>(a, k, knext, inv_bb, alpha, cdeg, sm, it, pass++);
+        column_pass<NR, BF16, kUpdateC, false, GEN>(a, cta, k, knext, inv_bb, alpha, cdeg, sm, it, pass++);
       if (rec) a.tstamp[4 * step + 2] = globaltimer_ns();
       DID_GRID_SYNC();
       if (rec) a.tstamp[4 * step + 3] = globaltimer_ns();
@@ -552,7 +556,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_kernel(SweepArgs a) {
     }
     __syncthreads();
     const double f = bc[3];
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (cta == 0 && threadIdx.x == 0) {
       a.trace[s] = f;
       a.ctrl->sweeps = s + 1;
     }
@@ -564,11 +568,28 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_kernel(SweepArgs a) {
     }
     f_prev = f;
     if (stop) {
-      if (blockIdx.x == 0 && threadIdx.x == 0) a.ctrl->stopped = 1;
+      if (cta == 0 && threadIdx.x == 0) a.ctrl->stopped = 1;
       break;
     }
   }
 #undef DID_GRID_SYNC
+}
+
+template <int NR, bool BF16>
+__global__ void __launch_bounds__(kSweepThreads, 1) sweep_kernel(SweepArgs a) {
+  sweep_body<NR, BF16, false>(a, blockIdx.x, gridDim.x);
+}
+
+// Several instances in one cooperative launch: instance i runs on CTAs
+// [cta_begin, cta_begin + cta_count) with its own counters and barriers.
+template <int NR, bool BF16>
+__global__ void __launch_bounds__(kSweepThreads, 1) sweep_multi_kernel(const SweepArgs* __restrict__ inst, int ninst) {
+  int i = 0;
+  while (i + 1 < ninst && (int)blockIdx.x >= inst[i + 1].cta_begin) ++i;
+  const SweepArgs a = inst[i];
+  const int cta = (int)blockIdx.x - a.cta_begin;
+  if (cta < 0 || cta >= a.cta_count) return;
+  sweep_body<NR, BF16, true>(a, cta, a.cta_count);
 }
 
 template <int NR, bool BF16>
@@ -703,6 +724,77 @@ did_status plan_sweep(int ld, int64_t N, bool bf16, int grid_override, int64_t m
   plan->units = U;
   plan->dynamic = dyn ? 1 : 0;
   return DID_OK;
+}
+
+// ------------------------------------------------------ multi-instance plan
+// One kernel variant (NR = kServeNr) serves instances of every shape up to
+// kSweepThreads * kServeNr * VR rows; each instance gets GS = the smallest
+// power of two with GS * kServeNr >= nvec, static column units (one per
+// group) and per-CTA partials, and the deepest ring that fits the launch's
+// shared memory.
+constexpr int kServeNr = 4;
+
+int serve_max_ld(bool bf16) { return kSweepThreads * kServeNr * (bf16 ? 8 : 4); }
+
+static const void* serve_func(bool bf16) {
+  return bf16 ? reinterpret_cast<const void*>(&sweep_multi_kernel<kServeNr, true>)
+              : reinterpret_cast<const void*>(&sweep_multi_kernel<kServeNr, false>);
+}
+
+did_status serve_launch_config(bool bf16, int* grid, size_t* smem_budget) {
+  int dev = 0, optin = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const void* f = serve_func(bf16);
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, f) != cudaSuccess) return DID_ECUDA;
+  const size_t budget = (size_t)optin - fa.sharedSizeBytes;
+  if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget) != cudaSuccess)
+    return DID_ECUDA;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, kSweepThreads, budget) != cudaSuccess ||
+      per_sm < 1)
+    return DID_ECUDA;
+  *grid = sms * per_sm;
+  *smem_budget = budget;
+  return DID_OK;
+}
+
+did_status plan_instance(int ld, int64_t N, bool bf16, int ncta, size_t smem_budget, SweepPlan* plan) {
+  const int VR = bf16 ? 8 : 4;
+  const int elem = bf16 ? 2 : 4;
+  const int nvec = ld / VR;
+  if (ld > serve_max_ld(bf16)) return DID_E_TOO_LARGE;
+  int GS = 32;
+  while (GS * kServeNr < nvec) GS *= 2;
+  plan->GS = GS;
+  plan->NR = (nvec + GS - 1) / GS;
+  plan->NG = kSweepThreads / GS;
+  plan->D = 0;
+  for (int D = 6; D >= 2; --D)
+    if (sweep_smem(ld, plan->NG, D, elem).total <= smem_budget) { plan->D = D; break; }
+  if (plan->D == 0) return DID_E_TOO_LARGE;
+  plan->smem = sweep_smem(ld, plan->NG, plan->D, elem).total;
+  plan->grid = ncta;
+  plan->func = serve_func(bf16);
+  const int64_t TG = (int64_t)ncta * plan->NG;
+  Units U{};
+  U.tg = TG;
+  U.c0 = (N + TG - 1) / TG;
+  U.n0 = N;
+  U.n1 = N;
+  U.c1 = U.c2 = 1;
+  plan->units = U;
+  plan->nunits = (int)TG;
+  plan->npart = ncta;
+  plan->dynamic = 0;
+  return DID_OK;
+}
+
+cudaError_t launch_sweep_multi(bool bf16, const SweepArgs* d_inst, int ninst, int grid, size_t smem, cudaStream_t s) {
+  const SweepArgs* inst = d_inst;
+  void* params[] = {(void*)&inst, (void*)&ninst};
+  return cudaLaunchCooperativeKernel(serve_func(bf16), dim3(grid), dim3(kSweepThreads), params, smem, s);
 }
 
 cudaError_t launch_sweep(const SweepPlan& plan, const SweepArgs& args, cudaStream_t s) {
