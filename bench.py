@@ -175,6 +175,36 @@ def cpu_baseline(workload):
 
 
 # ------------------------------------------------------------------ main
+def serve_bench(did, n_req, rate, precision, budget_gb=120.0, max_slots=64, round_sweeps=4):
+    """Submit the first n_req requests of the serving stream at their Poisson
+    arrival times; return throughput and latency percentiles."""
+    from synth import workloads as SW
+    shapes = [SW.request_shape(0, r) for r in range(n_req)]
+    arrivals = SW.arrival_times(0, n_req, rate)
+    srv = did.Server(int(budget_gb * (1 << 30)), precision=precision, max_slots=max_slots,
+                     round_sweeps=round_sweeps)
+    tickets = []
+    t0 = time.perf_counter()
+    for r, (m, n, k) in enumerate(shapes):
+        d = t0 + arrivals[r] - time.perf_counter()
+        if d > 0:
+            time.sleep(d)
+        tickets.append(srv.submit(m, n, k, SW.request_seed(0, r), max_iter=300, tol=1e-4))
+    results = [srv.wait(t) for t in tickets]
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    iters = [r["iters"] for r in results]
+    work = sum(2.0 * m * n * k * (4 if precision == did.DID_FP32 else 2) * it
+               for (m, n, k), it in zip(shapes, iters))
+    return {"requests": n_req, "rate_req_per_s": rate, "precision": "fp32" if precision == did.DID_FP32 else "bf16r",
+            "completed": st["completed"], "failed": st["failed"], "solves_per_s": st["solves_per_s"],
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "wall_s": wall, "peak_active": st["peak_active"],
+            "peak_gb": st["peak_bytes"] / 1e9, "rounds": st["rounds"], "busy_s": st["busy_s"],
+            "mean_sweeps": float(sum(iters)) / len(iters), "sweep_GBps": work / st["busy_s"] / 1e9 if st["busy_s"] else None,
+            "note": "saturated: offered work exceeds one GPU at this rate" if rate >= 50 else ""}
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -217,6 +247,12 @@ def main():
                     help="M,N,K override of the workload's sizes (same generator); for profiling small cases")
     ap.add_argument("--phases", action="store_true",
                     help="also report the per-k phase split of the last timed sweep (globaltimer stamps)")
+    ap.add_argument("--no-bf16", action="store_true", help="skip the BF16-R measurement on the same workload")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-requests", type=int, default=128,
+                    help="requests of the serving stream to run (4096 in the full stream)")
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrival rate, requests/s")
+    ap.add_argument("--serve-only", action="store_true", help="run only the serving measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -237,6 +273,13 @@ def main():
     import __graft_entry__
     __graft_entry__.build()
     import paper_1802_08938_gb300 as did
+
+    if args.serve_only:
+        out = [serve_bench(did, args.serve_requests, args.serve_rate, p)
+               for p in ((did.DID_BF16R,) if args.precision == "bf16r" else (did.DID_FP32,))]
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "serving": out}), flush=True)
+        return 0
 
     w = dict(WORKLOADS[args.workload])
     if args.shape:
@@ -323,6 +366,35 @@ def main():
     ctx.close()
     del ctx
 
+    bf16 = None
+    if not args.no_bf16 and prec == did.DID_FP32:
+        c16 = did.Context(X, M, N, K, seed=seed, precision=did.DID_BF16R, refresh_every=w["refresh_every"],
+                          init_scale=w["init_scale"], stream=stream)
+        for _ in range(args.warmup):
+            c16.sweep(1)
+        i0 = c16.info()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            c16.sweep(1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        i1 = c16.info()
+        ms16 = e0.elapsed_time(e1)
+        kms16 = i1["sweep_kernel_ms"] - i0["sweep_kernel_ms"]
+        ab16 = args.steps * 2.0 * K * M * N * 2 + (i1["prologue_launches"] - i0["prologue_launches"]) * M * N * 2.0
+        f16 = c16.objective()
+        c16.close()
+        v16 = ws * args.steps / (ms16 / 1000.0)
+        bf16 = {"value": v16, "unit": "sweeps/s", "ratio_vs_fp32": v16 / value,
+                "roofline_frac": ab16 / (kms16 / 1e3) / 1e9 / peak,
+                "tc_refreshes": int(i1["tc_refreshes"] - i0["tc_refreshes"]),
+                "objective_after": f16,
+                "note": "same workload and seed, R stored in bfloat16, tensor-core BF16x3 refresh"}
+        gpu_launches += args.steps + 3 * int(i1["tc_refreshes"] - i0["tc_refreshes"])
+
     e2e = None
     if not args.no_e2e:
         Xh = torch.empty((N, M), dtype=torch.float32, pin_memory=True)
@@ -352,6 +424,11 @@ def main():
     else:
         del X
 
+    serving = None
+    if not args.no_serve and not args.shape:
+        serving = [serve_bench(did, args.serve_requests, args.serve_rate, did.DID_FP32),
+                   serve_bench(did, args.serve_requests, args.serve_rate, did.DID_BF16R)]
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and not args.shape:
         cpu = cpu_baseline(args.workload)
@@ -375,6 +452,8 @@ def main():
             "gpu_launches": int(gpu_launches),
             "step_kernel_ms": step_ms,
             "refresh": refresh,
+            "bf16r": bf16,
+            "serving": serving,
             "phases": phases,
             "cpu_baseline": cpu,
             "clocks": clk,
