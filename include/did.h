@@ -280,8 +280,11 @@ typedef struct {
 } did_server_stats_t;
 
 /* max_slots: requests active at once (<= CTAs of one launch); round_sweeps:
- * sweeps per round (1..64; smaller admits sooner); stream: NULL = the server
- * creates its own. */
+ * the most sweeps a request runs in one round (1..64).  Within a round every
+ * request runs as many sweeps (up to round_sweeps) as fit in the time of the
+ * slowest request's single sweep (at least 5 ms), so all CTA ranges stay
+ * busy; a smaller round_sweeps admits new requests sooner.  stream: NULL =
+ * the server creates its own. */
 did_status did_server_create(size_t hbm_budget_bytes, did_precision precision, int32_t max_slots,
                              int32_t round_sweeps, void* stream, did_server** out);
 /* Queue a request (copied); *ticket identifies it.  DID_E_TOO_LARGE if it can

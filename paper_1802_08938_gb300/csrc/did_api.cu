@@ -479,7 +479,8 @@ did_status did_create_ex(const float* X, int64_t M, int64_t N, int32_t K, uint64
     return DID_EINVAL;
   did_options o;
   if (opt) o = *opt; else did_default_options(&o);
-  if ((o.precision != DID_FP32 && o.precision != DID_BF16R) || (o.order != DID_ORDER_INTERLEAVED) ||
+  if ((o.precision != DID_FP32 && o.precision != DID_BF16R) ||
+      (o.order != DID_ORDER_INTERLEAVED && o.order != DID_ORDER_DID) ||
       (o.stop != DID_STOP_RELCHANGE && o.stop != DID_STOP_PAPER_EPS) || o.refresh_every < 0 ||
       o.debug_barrier_extra < 0 || (o.flags & ~(DID_FLAG_PHASE_TIMES | DID_FLAG_SIMT_REFRESH)))
     return DID_EINVAL;

@@ -28,6 +28,12 @@ using did::SweepArgs;
 namespace {
 
 constexpr uint64_t kServeTimeoutNs = 4000000000ull;
+// Cost model of one column pass of an instance on s CTAs (used to balance a
+// round): a fixed part (two grid waits, the b-reduce, the ring's fill) plus
+// the residual's read and write at one CTA's share of the HBM bandwidth.
+constexpr double kPassFixedS = 12e-6;
+constexpr double kCtaBytesPerS = 40e9;
+constexpr double kRoundMinS = 5e-3;      // a round lasts at least this long
 
 double now_s(const std::chrono::steady_clock::time_point& t0) {
   return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -221,6 +227,22 @@ std::vector<int> shares(const did_server* s, const std::vector<Req*>& act) {
 bool run_round(did_server* s, std::vector<Req*>& act) {
   const int n = (int)act.size();
   const std::vector<int> sh = shares(s, act);
+  // Sweeps per instance: the round lasts about as long as the slowest
+  // instance's single sweep (at least kRoundMinS); faster instances run more
+  // sweeps in that time, so no CTA range idles for long.
+  std::vector<double> tsw(n);
+  double T = kRoundMinS;
+  for (int i = 0; i < n; ++i) {
+    const Req* r = act[i];
+    const double pass_bytes = 2.0 * (double)r->ld * (double)r->rq.N * (s->bf16 ? 2.0 : 4.0);
+    tsw[i] = (double)r->rq.K * (kPassFixedS + pass_bytes / ((double)sh[i] * kCtaBytesPerS));
+    T = std::max(T, tsw[i]);
+  }
+  std::vector<int> nsw(n);
+  for (int i = 0; i < n; ++i) {
+    const int left = act[i]->rq.max_iter - act[i]->sweeps;
+    nsw[i] = std::max(1, std::min(std::min(s->round_sweeps, left), (int)(T / tsw[i])));
+  }
   size_t smem = 0;
   int begin = 0;
   for (int i = 0; i < n; ++i) {
@@ -251,7 +273,7 @@ bool run_round(did_server* s, std::vector<Req*>& act) {
     a.nunits = plan.nunits;
     a.dynamic = 0;
     a.npart = plan.npart;
-    a.n_sweeps = std::min(s->round_sweeps, r->rq.max_iter - r->sweeps);
+    a.n_sweeps = nsw[i];
     a.prologue = 1;          // the CTA split may change between rounds
     a.f_prev = r->trace.back();
     a.f0 = r->trace.front();

@@ -33,7 +33,12 @@ namespace did {
 
 namespace {
 
-enum PassMode { kPrologue = 0, kUpdateC = 1 };
+// Column-pass modes.
+//   kPrologue: partials of R c_knext^T only (no store).
+//   kUpdateC:  c_k update from b_k' (sb) and the previous b_k (bo), R written.
+//   kWriteB:   c_k kept; R += (b_k - b_k') c_k written (the B step of the
+//              C-first order, Algorithm 2 / Section 4.2 E := E - delta b c).
+enum PassMode { kPrologue = 0, kUpdateC = 1, kWriteB = 2 };
 
 constexpr int kMaxNrF32 = 10;   // 16-byte vectors per thread and column
 constexpr int kMaxNrBf16 = 5;
@@ -164,7 +169,7 @@ __device__ __forceinline__ void column_pass(const SweepArgs& a, int cta, int k, 
     for (int e = 0; e < VR; e += 4) {
       if (!BF16) {
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (MODE == kUpdateC && ok) v = __ldcg(reinterpret_cast<const float4*>(a.B + (size_t)k * ld + q * VR + e));
+        if (MODE != kPrologue && ok) v = __ldcg(reinterpret_cast<const float4*>(a.B + (size_t)k * ld + q * VR + e));
         bn[BF16 ? 0 : r][e / 2] = make_float2(v.x, v.y);
         bn[BF16 ? 0 : r][e / 2 + 1] = make_float2(v.z, v.w);
       }
@@ -267,10 +272,10 @@ __device__ __forceinline__ void column_pass(const SweepArgs& a, int cta, int k, 
       unit_range(UN, N, cu, cu_lo, cu_hi);
     }
     if (j != pf_j) {                        // no prefetch for this column (a unit's start)
-      if (MODE == kUpdateC) co0 = __ldcg(Ck + j);
+      if (MODE != kPrologue) co0 = __ldcg(Ck + j);
       cn0 = __ldcg(Cn + j);
       if (j + 1 < cu_hi) {
-        if (MODE == kUpdateC) co1 = __ldcg(Ck + j + 1);
+        if (MODE != kPrologue) co1 = __ldcg(Ck + j + 1);
         cn1 = __ldcg(Cn + j + 1);
       }
     }
@@ -279,7 +284,7 @@ __device__ __forceinline__ void column_pass(const SweepArgs& a, int cta, int k, 
     co0 = co1;
     cn0 = cn1;
     if (j + 2 < cu_hi) {                    // c_kj and c_{knext,j} two columns ahead
-      if (MODE == kUpdateC) co1 = __ldcg(Ck + j + 2);
+      if (MODE != kPrologue) co1 = __ldcg(Ck + j + 2);
       cn1 = __ldcg(Cn + j + 2);
     }
     pf_j = j + 1;
@@ -336,7 +341,7 @@ __device__ __forceinline__ void column_pass(const SweepArgs& a, int cta, int k, 
         const int q = lt + r * GS;
         float f[VR];
         V::unpack(stage[r * GS], f);
-        if (MODE == kUpdateC) {
+        if (MODE != kPrologue) {
 #pragma unroll
           for (int e = 0; e < VR; e += 4) {
             // BF16: the 8 previous-b values of vector q are stored as two
@@ -366,7 +371,7 @@ __device__ __forceinline__ void column_pass(const SweepArgs& a, int cta, int k, 
   }
   flush(cu);
   // R written here is read by TMA (async proxy) in the next pass.
-  if (MODE == kUpdateC) fence_proxy_async_global();
+  if (MODE != kPrologue) fence_proxy_async_global();
 
   if (!a.dynamic) {
     // Static units: partials per CTA -- groups -> shared memory -> row sums in
@@ -402,10 +407,13 @@ __device__ __forceinline__ void column_pass(const SweepArgs& a, int cta, int k, 
 
 // b-reduce for block k: s = sum over the partial rows of P (fixed order), b_k'
 // from the closed form, ||b_k'||^2 and b_k'.b_k partials of this CTA's row
-// slice.  The slice's rows are spread over the CTA's threads together with
-// interleaved subsets of the partial rows (up to 16 loads in flight each);
-// the subsets' sums are added in subset order.
-__device__ __forceinline__ void b_reduce(const SweepArgs& a, int cta, int G, int k, float* acc, double* bc) {
+// slice.  Each round covers `rows` rows of the slice with S = min(16, npart)
+// interleaved subsets of the partial rows per row (thread t: row t % rows,
+// subset t / rows, up to 16 loads in flight); the subsets' sums are added in
+// subset order, then one thread per row forms b_k'.  With few partial rows
+// (an instance on few CTAs) a round covers up to 512 rows.
+__device__ __forceinline__ void b_reduce(const SweepArgs& a, int cta, int G, int k, float* acc, double* bc,
+                                         double* dscr) {
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   const int U = a.npart;
   if (w == 0) {
@@ -416,34 +424,35 @@ __device__ __forceinline__ void b_reduce(const SweepArgs& a, int cta, int G, int
   const int r0 = cta * rpc;
   const int r1 = min(a.ld, r0 + rpc);
   const int nrows = max(0, r1 - r0);
+  int S = 1;
+  while (S < 16 && S < U) S *= 2;
+  const int per_round = kSweepThreads / S;
   double bb = 0.0, bob = 0.0;
-  // rows handled per round: at most 32 (one per lane of warp 0 in the epilogue)
-  for (int c0 = 0; c0 < nrows; c0 += 32) {
-    const int rows = min(32, nrows - c0);
-    const int lanes = kSweepThreads / rows;          // subsets per row (>= 16)
+  for (int c0 = 0; c0 < nrows; c0 += per_round) {
+    const int rows = min(per_round, nrows - c0);
     const int t = threadIdx.x;
-    const int rr = t % rows, sub = t / rows;
+    const int rr = t % per_round, sub = t / per_round;
     float s = 0.f;
-    if (sub < lanes) {
+    if (rr < rows) {
       const int row = r0 + c0 + rr;
-      for (int gi0 = sub; gi0 < U; gi0 += 16 * lanes) {
+      for (int gi0 = sub; gi0 < U; gi0 += 16 * S) {
         float v[16];
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
-          const int gi = gi0 + u * lanes;
+          const int gi = gi0 + u * S;
           v[u] = gi < U ? __ldcg(a.P + (size_t)gi * a.ld + row) : 0.f;
         }
 #pragma unroll
         for (int u = 0; u < 16; ++u) s += v[u];
       }
     }
-    acc[t] = s;                                       // acc[sub * rows + rr]
+    acc[t] = s;                                       // acc[sub * per_round + rr]
     __syncthreads();
     const double cc = bc[0];
-    if (w == 0 && l < rows) {
-      const int row = r0 + c0 + l;
+    if (t < rows) {
+      const int row = r0 + c0 + t;
       float tot = 0.f;
-      for (int sb = 0; sb < lanes; ++sb) tot += acc[sb * rows + l];
+      for (int sb = 0; sb < S; ++sb) tot += acc[sb * per_round + t];
       const float b_old = __ldcg(a.B + (size_t)k * a.ld + row);
       float b_new = b_old;
       if (cc > 0.0) {
@@ -457,15 +466,12 @@ __device__ __forceinline__ void b_reduce(const SweepArgs& a, int cta, int G, int
     }
     __syncthreads();
   }
-  __syncthreads();
+  bb = block_sum_f64(bb, dscr);
+  bob = block_sum_f64(bob, dscr);
   const double cc = bc[0];
-  if (w == 0) {
-    bb = warp_sum_f64(bb);
-    bob = warp_sum_f64(bob);
-    if (l == 0) {
-      __stcg(a.Sp + 2 * cta, bb);
-      __stcg(a.Sp + 2 * cta + 1, bob);
-    }
+  if (threadIdx.x == 0) {
+    __stcg(a.Sp + 2 * cta, bb);
+    __stcg(a.Sp + 2 * cta + 1, bob);
   }
   if (!(cc > 0.0) && cta == 0 && threadIdx.x == 0) atomicAdd(a.degen, 1ull);
 }
@@ -504,20 +510,96 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a, int cta, int ncta
       return;                                                                            \
   } while (0)
 
+  // Shared copies of the previous b (bo) and, for a BF16 residual, of b' (bnw)
+  // in the half-plane layout: element e of 8-row vector q at (e/4)*ld/2 + q*4 + e%4.
+  // Returns sum_i src_b'^2 in float64 (same order in every CTA).
+  auto stage_b = [&](const float* src_old, const float* src_new) -> double {
+    double nn = 0.0;
+    if (BF16) {
+      for (int i = threadIdx.x; i < a.ld; i += blockDim.x) {
+        const int dst = ((i & 7) >> 2) * (a.ld / 2) + (i >> 3) * 4 + (i & 3);
+        const float vn = __ldcg(src_new + i);
+        sm.bo[dst] = __ldcg(src_old + i);
+        sm.bnw[dst] = vn;
+        nn += (double)vn * (double)vn;
+      }
+    } else {
+      for (int i = threadIdx.x; i < a.ld; i += blockDim.x) {
+        sm.bo[i] = __ldcg(src_old + i);
+        const float vn = __ldcg(src_new + i);
+        nn += (double)vn * (double)vn;
+      }
+    }
+    return block_sum_f64(nn, sm.dscr);   // includes the barrier before the pass
+  };
+
+  const double f0 = a.f0;
+  double f_prev = a.f_prev;
+  const bool stamps = a.tstamp != nullptr && cta == 0 && threadIdx.x == 0;
+
+  if (a.order == DID_ORDER_DID) {
+    // C-first order (Algorithm 2; Algorithm 3 takes the same blocks): the C
+    // step visits c_1..c_K with b fixed (equations up:c), the B step b_1..b_K
+    // with C fixed (sol:b_i, E := E - delta b_i c_i).  Partials for b_1 come
+    // from the last C pass, so no prologue is needed.
+    for (int s = 0; s < a.n_sweeps; ++s) {
+      for (int k = 0; k < a.K; ++k) {
+        const float* bk = a.B + (size_t)k * a.ld;
+        const double bb = stage_b(bk, bk);
+        const bool cdeg = !(bb > 0.0);
+        if (cdeg && cta == 0 && threadIdx.x == 0) atomicAdd(a.degen, 1ull);
+        const float inv_bb = cdeg ? 0.f : (float)(1.0 / bb);
+        column_pass<NR, BF16, kUpdateC, false, GEN>(a, cta, k, k + 1 < a.K ? k + 1 : 0, inv_bb, 1.f, cdeg, sm,
+                                                    it, pass++);
+        DID_GRID_SYNC();
+      }
+      for (int k = 0; k < a.K; ++k) {
+        b_reduce(a, cta, G, k, sm.red, bc, sm.dscr);
+        DID_GRID_SYNC();
+        stage_b(a.bold, a.B + (size_t)k * a.ld);
+        const int knext = k + 1 < a.K ? k + 1 : 0;
+        if (k == a.K - 1)
+          column_pass<NR, BF16, kWriteB, true, GEN>(a, cta, k, knext, 0.f, 0.f, true, sm, it, pass++);
+        else
+          column_pass<NR, BF16, kWriteB, false, GEN>(a, cta, k, knext, 0.f, 0.f, true, sm, it, pass++);
+        DID_GRID_SYNC();
+      }
+      if (w == 0) {
+        const double o = warp_sum_global_f64(a.OBJp, a.npart, 1);
+        if (l == 0) bc[3] = 0.5 * o;
+      }
+      __syncthreads();
+      const double f = bc[3];
+      if (cta == 0 && threadIdx.x == 0) {
+        a.trace[s] = f;
+        a.ctrl->sweeps = s + 1;
+      }
+      bool stop = false;
+      if (a.stop_rule == 1) {
+        stop = (f == 0.0) || (f_prev > 0.0 && fabs(f_prev - f) / f_prev < a.tol);
+      } else if (a.stop_rule == 2) {
+        stop = f <= a.tol * f0;
+      }
+      f_prev = f;
+      if (stop) {
+        if (cta == 0 && threadIdx.x == 0) a.ctrl->stopped = 1;
+        break;
+      }
+    }
+    return;
+  }
+
   if (a.prologue) {
     column_pass<NR, BF16, kPrologue, false, GEN>(a, cta, 0, 0, 0.f, 0.f, true, sm, it, pass++);
     DID_GRID_SYNC();
   }
-  const double f0 = a.f0;
-  double f_prev = a.f_prev;
 
-  const bool stamps = a.tstamp != nullptr && cta == 0 && threadIdx.x == 0;
   for (int s = 0; s < a.n_sweeps; ++s) {
     for (int k = 0; k < a.K; ++k) {
       const int step = s * a.K + k;
       const bool rec = stamps && step < a.tstamp_cap;
       if (rec) a.tstamp[4 * step + 0] = globaltimer_ns();
-      b_reduce(a, cta, G, k, sm.red, bc);
+      b_reduce(a, cta, G, k, sm.red, bc, sm.dscr);
       DID_GRID_SYNC();
       if (rec) a.tstamp[4 * step + 1] = globaltimer_ns();
       if (w == 0) {
@@ -525,17 +607,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a, int cta, int ncta
         const double bob = warp_sum_global_f64(a.Sp + 1, G, 2);
         if (l == 0) { bc[1] = bb; bc[2] = bob; }
       }
-      if (BF16) {
-        // half planes: element e of 8-row vector q -> (e/4)*ld/2 + q*4 + e%4
-        for (int i = threadIdx.x; i < a.ld; i += blockDim.x) {
-          const int dst = ((i & 7) >> 2) * (a.ld / 2) + (i >> 3) * 4 + (i & 3);
-          sm.bo[dst] = __ldcg(a.bold + i);
-          sm.bnw[dst] = __ldcg(a.B + (size_t)k * a.ld + i);
-        }
-      } else {
-        for (int i = threadIdx.x; i < a.ld; i += blockDim.x) sm.bo[i] = __ldcg(a.bold + i);
-      }
-      __syncthreads();
+      stage_b(a.bold, a.B + (size_t)k * a.ld);
       const double bb = bc[1], bob = bc[2];
       const bool cdeg = !(bb > 0.0);
       const float inv_bb = cdeg ? 0.f : (float)(1.0 / bb);
