@@ -42,6 +42,10 @@ WORKLOADS = {
                                          sigma=0.01, salt_frac=0.0, refresh_every=0, init_scale=False),
 }
 DEFAULT_WORKLOAD = "planted_exp_5000x200000_k50"
+# Block orders (did_options.order): per-k interleaved, per-k C-first, batched Algorithm 3.
+ORDERS = {"interleaved": 0, "did": 1, "did_batched": 2}
+# float32 FMA peak of the SIMT pipes: 152 SMs x 128 lanes x 2 flops x 2070 MHz (maximum SM clock)
+FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # Column slice of each workload for the oracle timing (about 10-20 s of CPU work).
 CPU_SAMPLE_COLS = {"planted_exp_5000x200000_k50": 1000, "image_like_784x70000_k16": 4000,
                    "salt_10000x500000_k100": 250, "planted_uniform_200x1000_k10": 1000}
@@ -205,6 +209,46 @@ def serve_bench(did, n_req, rate, precision, budget_gb=120.0, max_slots=64, roun
             "note": "saturated: offered work exceeds one GPU at this rate" if rate >= 50 else ""}
 
 
+def batched_flops(M, N, K):
+    """Algorithmic float32 flops of one batched sweep of Algorithm 3 with a
+    pending correction: g = B^T R (2KMN), R -= [D B][C_old; dl] (4KMN),
+    W = R C^T (2KMN), the K x K products and the per-column / per-row solves."""
+    return 8.0 * K * M * N + 2.0 * K * K * N * 2 + 2.0 * (2 * K) ** 2 * M + 2.0 * K * K * (N + M)
+
+
+def order_bench(did, X, M, N, K, w, seed, stream, order, steps, warmup):
+    """Sweeps/s of one block order on the same workload, seed and start."""
+    import torch
+    c = did.Context(X, M, N, K, seed=seed, precision=did.DID_FP32, order=ORDERS[order],
+                    refresh_every=w["refresh_every"], init_scale=w["init_scale"], stream=stream)
+    for _ in range(warmup):
+        c.sweep(1)
+    i0 = c.info()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        c.sweep(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    i1 = c.info()
+    ms = e0.elapsed_time(e1)
+    f = c.objective()
+    c.close()
+    out = {"order": order, "value": steps / (ms / 1000.0), "unit": "sweeps/s", "ms_per_sweep": ms / steps,
+           "objective_after": f, "sweeps": warmup + steps,
+           "sweep_ms": (i1["sweep_kernel_ms"] - i0["sweep_kernel_ms"]) / steps}
+    if order == "did_batched":
+        fl = batched_flops(M, N, K)
+        out["roofline"] = {"bound": "alu", "achieved": fl / (out["sweep_ms"] / 1e3) / 1e12,
+                           "peak": FP32_SIMT_TFLOPS, "unit": "TFLOP/s",
+                           "frac": fl / (out["sweep_ms"] / 1e3) / 1e12 / FP32_SIMT_TFLOPS,
+                           "flops_per_sweep": fl, "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                           "note": "whole sweep (cuBLAS SGEMMs + solve/update/norm kernels)"}
+    return out
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -245,6 +289,11 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16r"])
     ap.add_argument("--shape", default=None,
                     help="M,N,K override of the workload's sizes (same generator); for profiling small cases")
+    ap.add_argument("--order", default="interleaved", choices=sorted(ORDERS),
+                    help="block order of the main line: per-k interleaved (Section 4.1), per-k C-first "
+                         "(Algorithm 2), or the batched form of Algorithm 3")
+    ap.add_argument("--no-orders", action="store_true",
+                    help="skip the C-first and batched Algorithm 3 measurements on the same workload")
     ap.add_argument("--phases", action="store_true",
                     help="also report the per-k phase split of the last timed sweep (globaltimer stamps)")
     ap.add_argument("--no-bf16", action="store_true", help="skip the BF16-R measurement on the same workload")
@@ -302,8 +351,10 @@ def main():
         if ws > 1:
             torch.distributed.barrier()
 
-    ctx = did.Context(X, M, N, K, seed=seed, precision=prec, refresh_every=w["refresh_every"],
-                      init_scale=w["init_scale"], stream=stream,
+    if args.order == "did_batched" and prec != did.DID_FP32:
+        ap.error("the batched order runs in float32 only")
+    ctx = did.Context(X, M, N, K, seed=seed, precision=prec, order=ORDERS[args.order],
+                      refresh_every=w["refresh_every"], init_scale=w["init_scale"], stream=stream,
                       flags=did.DID_FLAG_PHASE_TIMES if args.phases else 0)
     for _ in range(args.warmup):
         ctx.sweep(1)
@@ -395,6 +446,15 @@ def main():
                 "note": "same workload and seed, R stored in bfloat16, tensor-core BF16x3 refresh"}
         gpu_launches += args.steps + 3 * int(i1["tc_refreshes"] - i0["tc_refreshes"])
 
+    orders = None
+    if not args.no_orders and prec == did.DID_FP32 and args.order == "interleaved":
+        orders = [order_bench(did, X, M, N, K, w, seed, stream, o, args.steps, args.warmup)
+                  for o in ("did", "did_batched")]
+        for o in orders:
+            o["ratio_vs_main"] = o["value"] / value
+        # the batched form runs 4 of the library's kernels per sweep next to cuBLAS SGEMMs
+        gpu_launches += args.steps + 4 * args.steps
+
     e2e = None
     if not args.no_e2e:
         Xh = torch.empty((N, M), dtype=torch.float32, pin_memory=True)
@@ -433,6 +493,20 @@ def main():
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and not args.shape:
         cpu = cpu_baseline(args.workload)
 
+    if args.order == "did_batched":
+        fl = batched_flops(M, N, K) * args.steps
+        roofline = {"bound": "alu", "achieved": fl / (kms / 1e3) / 1e12, "peak": FP32_SIMT_TFLOPS,
+                    "unit": "TFLOP/s", "frac": fl / (kms / 1e3) / 1e12 / FP32_SIMT_TFLOPS, "traffic": None,
+                    "kernel": "batched sweep (cuBLAS SGEMMs + solve/update/norm kernels)",
+                    "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                    "flops_per_sweep": batched_flops(M, N, K), "kernel_ms_per_sweep": kms / max(1, args.steps)}
+    else:
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": traffic if args.order == "interleaved" else None,
+                    "kernel": "sweep_kernel", "peak_kind": peak_kind,
+                    "alg_bytes_per_sweep": 2.0 * K * M * N * s_bytes,
+                    "kernel_ms_per_sweep": kms / max(1, args.steps)}
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": ws, "steps": args.steps,
@@ -440,19 +514,17 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == did.DID_FP32 else "bf16-storage/f32",
             "data": "synthetic",
             "config": {"workload": args.workload, "M": M, "N": N, "K": K, "precision": args.precision,
+                       "order": args.order,
                        "refresh_every": w["refresh_every"], "init_scale": w["init_scale"],
                        "l2": "inputs larger than L2 (R is %.1f GB)" % (M * N * s_bytes / 1e9),
                        "parallelism": "replicas" if ws > 1 else "single"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "sweep_kernel", "peak_kind": peak_kind,
-                         "alg_bytes_per_sweep": 2.0 * K * M * N * s_bytes,
-                         "kernel_ms_per_sweep": kms / max(1, args.steps)},
+            "roofline": roofline,
             "e2e": e2e,
             "gpu_launches": int(gpu_launches),
             "step_kernel_ms": step_ms,
             "refresh": refresh,
             "bf16r": bf16,
+            "orders": orders,
             "serving": serving,
             "phases": phases,
             "cpu_baseline": cpu,

@@ -58,7 +58,17 @@ typedef enum { DID_FP32 = 0, DID_BF16R = 1 } did_precision;
  *   residue order of HALS (Section 2, HALS closed forms).
  * DID_ORDER_DID: c_1..c_K then b_1..b_K -- the order of DBCD and DID
  *   (Algorithms 2 and 3).  Both apply the same exact block minimisers. */
-typedef enum { DID_ORDER_INTERLEAVED = 0, DID_ORDER_DID = 1 } did_order;
+/* DID_ORDER_DID_BATCHED: the same C-first order in the batched form of
+ *   Algorithm 3 (Section 4.2): each sweep forms g = B^T E for all columns and
+ *   solves the K successive c updates per column with G = B^T B, updates the
+ *   residual by one rank-2K product, then takes W = E C^T and V = C C^T in a
+ *   single reduction and applies b_i := [b_i + w_i/v_ii - sum_{k<i}
+ *   (v_ik/v_ii) delta b_k]_+; the delta b correction of R is applied lazily
+ *   by the next sweep.  Float32 residual only, K <= 128 (did_create_ex
+ *   returns DID_EINVAL otherwise).  The objective of each sweep is the
+ *   float64 norm of the residual after the C step, with the B step's change
+ *   taken from an exact float64 identity in W, V and delta b. */
+typedef enum { DID_ORDER_INTERLEAVED = 0, DID_ORDER_DID = 1, DID_ORDER_DID_BATCHED = 2 } did_order;
 
 /* Stopping rule of did_factor.
  * DID_STOP_RELCHANGE: |f_{t-1} - f_t| / f_{t-1} < tol, or f_t == 0.

@@ -26,7 +26,7 @@ LIB_PATH = os.path.join(_HERE, "libdid.so")
 DID_OK, DID_PENDING, DID_EINVAL, DID_ENOMEM, DID_ECUDA, DID_ETIMEOUT, DID_E_TOO_LARGE, DID_EBUSY = (
     0, 1, -1, -2, -3, -4, -5, -6)
 DID_FP32, DID_BF16R = 0, 1
-DID_ORDER_INTERLEAVED, DID_ORDER_DID = 0, 1
+DID_ORDER_INTERLEAVED, DID_ORDER_DID, DID_ORDER_DID_BATCHED = 0, 1, 2
 DID_STOP_RELCHANGE, DID_STOP_PAPER_EPS = 0, 1
 DID_FLAG_PHASE_TIMES = 1
 DID_FLAG_SIMT_REFRESH = 2

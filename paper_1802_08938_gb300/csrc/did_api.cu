@@ -29,7 +29,8 @@ struct did_ctx {
 
   float* X = nullptr;
   void* R = nullptr;
-  float* B = nullptr;
+  float* Y = nullptr;               // [D | B]: pending delta b (batched order) and B, ld x 2K
+  float* B = nullptr;               // = Y + K*ld
   float* C = nullptr;
   float* P = nullptr;
   double* CCp = nullptr;
@@ -41,6 +42,7 @@ struct did_ctx {
   unsigned long long* degen = nullptr;
   double* dense_part = nullptr;
   unsigned long long* bad = nullptr;
+  did::BatchedState* batched = nullptr;   // DID_ORDER_DID_BATCHED
   void* tc_ws = nullptr;            // tensor-core refresh operands (allocated on first use)
   double* tc_part = nullptr;        // per-CTA sums of the tensor-core refresh
   int* tc_err = nullptr;
@@ -116,6 +118,8 @@ did_status host_alloc(did_ctx* c, void** p, size_t bytes) {
 }
 
 void free_all(did_ctx* c) {
+  did::batched_destroy(c->batched);
+  c->batched = nullptr;
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   c->ev0 = c->ev1 = nullptr;
@@ -230,6 +234,7 @@ did_status refresh(did_ctx* c) {
     if (st != DID_OK) return st;
   }
   c->last_obj = 0.5 * s[0];
+  if (c->batched) DID_CUDA(c, did::batched_reset(c->batched, c->Y, c->ld, c->K, s[0], c->stream));
   c->need_prologue = true;
   c->need_refresh = false;
   c->last_refresh_at = c->sweeps_done;
@@ -322,7 +327,45 @@ int chunk_size(const did_ctx* c, int64_t remaining) {
   return (int)std::max<int64_t>(1, chunk);
 }
 
+// Batched order: sweeps of GEMMs and small kernels on the context's stream.
+did_status run_batched(did_ctx* c, int64_t max_sweeps, int stop_rule, double tol, int64_t* done_total) {
+  *done_total = 0;
+  while (*done_total < max_sweeps) {
+    if (refresh_due(c)) {
+      did_status st = refresh(c);
+      if (st != DID_OK) return st;
+    }
+    const int chunk = chunk_size(c, max_sweeps - *done_total);
+    const int n = stop_rule ? 1 : chunk;     // with a stopping rule: one sweep per check
+    DID_CUDA(c, cudaEventRecord(c->ev0, c->stream));
+    for (int s = 0; s < n; ++s)
+      DID_CUDA(c, did::batched_sweep(c->batched, (float*)c->R, c->Y, c->C, c->ld, c->N, c->K, c->degen,
+                                     c->trace_dev + s, c->stream));
+    DID_CUDA(c, cudaEventRecord(c->ev1, c->stream));
+    DID_CUDA(c, cudaMemcpyAsync(c->trace_host, c->trace_dev, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+    DID_CUDA(c, cudaStreamSynchronize(c->stream));
+    float ms = 0.f;
+    DID_CUDA(c, cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    c->sweep_ms += ms;
+    c->sweep_launches += n;
+    bool stopped = false;
+    for (int s = 0; s < n; ++s) {
+      const double f = c->trace_host[s];
+      const double prev = c->trace.back();
+      c->trace.push_back(f);
+      c->sweeps_done++;
+      (*done_total)++;
+      if (stop_rule == 1 && (f == 0.0 || (prev > 0.0 && fabs(prev - f) / prev < tol))) stopped = true;
+      if (stop_rule == 2 && f <= tol * c->trace.front()) stopped = true;
+    }
+    c->last_obj = c->trace.back();
+    if (stopped) break;
+  }
+  return DID_OK;
+}
+
 did_status run(did_ctx* c, int64_t max_sweeps, int stop_rule, double tol, int64_t* done_total) {
+  if (c->batched) return run_batched(c, max_sweeps, stop_rule, tol, done_total);
   *done_total = 0;
   while (*done_total < max_sweeps) {
     if (refresh_due(c)) {
@@ -403,7 +446,9 @@ static did_status create_impl(did_ctx* c, const float* X, uint64_t seed) {
   } while (0)
   ALLOC(X, elems * sizeof(float));
   ALLOC(R, elems * (c->bf16 ? 2 : 4));
-  ALLOC(B, (size_t)c->ld * K * sizeof(float));
+  ALLOC(Y, (size_t)c->ld * 2 * K * sizeof(float));
+  c->B = c->Y + (size_t)K * c->ld;
+  DID_CUDA(c, cudaMemsetAsync(c->Y, 0, (size_t)c->ld * K * sizeof(float), c->stream));
   ALLOC(C, (size_t)K * N * sizeof(float));
   const size_t U = (size_t)std::max(c->plan.npart, G);
   ALLOC(P, U * c->ld * sizeof(float));
@@ -421,6 +466,12 @@ static did_status create_impl(did_ctx* c, const float* X, uint64_t seed) {
     ALLOC(tstamp, sizeof(uint64_t) * 4 * c->tstamp_cap);
   }
 #undef ALLOC
+  if (c->opt.order == DID_ORDER_DID_BATCHED) {
+    st = dev_alloc(c, &p, did::batched_workspace_bytes(c->ld, N, K));
+    if (st != DID_OK) return st;
+    c->batched = did::batched_create(p, c->ld, N, K, c->stream);
+    if (!c->batched) return fail(c, DID_ECUDA, "cuBLAS handle creation failed");
+  }
   st = host_alloc(c, &p, sizeof(Ctrl));
   if (st != DID_OK) return st;
   c->ctrl_host = (Ctrl*)p;
@@ -480,7 +531,8 @@ did_status did_create_ex(const float* X, int64_t M, int64_t N, int32_t K, uint64
   did_options o;
   if (opt) o = *opt; else did_default_options(&o);
   if ((o.precision != DID_FP32 && o.precision != DID_BF16R) ||
-      (o.order != DID_ORDER_INTERLEAVED && o.order != DID_ORDER_DID) ||
+      (o.order != DID_ORDER_INTERLEAVED && o.order != DID_ORDER_DID && o.order != DID_ORDER_DID_BATCHED) ||
+      (o.order == DID_ORDER_DID_BATCHED && (o.precision != DID_FP32 || !did::batched_supported(K))) ||
       (o.stop != DID_STOP_RELCHANGE && o.stop != DID_STOP_PAPER_EPS) || o.refresh_every < 0 ||
       o.debug_barrier_extra < 0 || (o.flags & ~(DID_FLAG_PHASE_TIMES | DID_FLAG_SIMT_REFRESH)))
     return DID_EINVAL;
@@ -568,6 +620,7 @@ did_status did_set_factors(did_ctx* c, const float* B, const float* C) {
 
 did_status did_get_residual(did_ctx* c, float* R) {
   if (!c || !R) return DID_EINVAL;
+  if (c->batched) DID_CUDA(c, did::batched_materialize(c->batched, (float*)c->R, c->Y, c->C, c->ld, c->N, c->K, c->stream));
   if (!c->bf16) {
     DID_CUDA(c, cudaMemcpy2DAsync(R, (size_t)c->M * sizeof(float), c->R, (size_t)c->ld * sizeof(float),
                                   (size_t)c->M * sizeof(float), (size_t)c->N, cudaMemcpyDefault, c->stream));

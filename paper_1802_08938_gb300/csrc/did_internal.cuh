@@ -352,6 +352,18 @@ int refresh_tc_grid();
 cudaError_t launch_refresh_tc(const float* X, void* R, const float* B, const float* C, int M, int ld, int64_t N,
                               int K, void* workspace, double* part, int* err, uint64_t timeout_ns, cudaStream_t s);
 
+// Batched DID (Algorithm 3 with one reduction per sweep; cuBLAS GEMMs).
+struct BatchedState;
+bool batched_supported(int K);
+size_t batched_workspace_bytes(int ld, int64_t N, int K);
+BatchedState* batched_create(void* ws, int ld, int64_t N, int K, cudaStream_t s);
+void batched_destroy(BatchedState* b);
+cudaError_t batched_reset(BatchedState* b, float* Y, int ld, int K, double e2, cudaStream_t s);
+cudaError_t batched_sweep(BatchedState* b, float* R, float* Y, float* C, int ld, int64_t N, int K,
+                          unsigned long long* degen, double* trace_out, cudaStream_t s);
+cudaError_t batched_materialize(BatchedState* b, float* R, float* Y, const float* C, int ld, int64_t N, int K,
+                                cudaStream_t s);
+
 // Generators.
 cudaError_t launch_gen_uniform_padded(float* out, int rows, int ld, int cols, uint64_t seed,
                                       int stream_id, cudaStream_t s);  // out[c*ld + r] = word c*rows + r
