@@ -216,11 +216,11 @@ def batched_flops(M, N, K):
     return 8.0 * K * M * N + 2.0 * K * K * N * 2 + 2.0 * (2 * K) ** 2 * M + 2.0 * K * K * (N + M)
 
 
-def order_bench(did, X, M, N, K, w, seed, stream, order, steps, warmup):
+def order_bench(did, X, M, N, K, w, seed, stream, order, steps, warmup, flags=0):
     """Sweeps/s of one block order on the same workload, seed and start."""
     import torch
     c = did.Context(X, M, N, K, seed=seed, precision=did.DID_FP32, order=ORDERS[order],
-                    refresh_every=w["refresh_every"], init_scale=w["init_scale"], stream=stream)
+                    refresh_every=w["refresh_every"], init_scale=w["init_scale"], stream=stream, flags=flags)
     for _ in range(warmup):
         c.sweep(1)
     i0 = c.info()
@@ -236,17 +236,34 @@ def order_bench(did, X, M, N, K, w, seed, stream, order, steps, warmup):
     ms = e0.elapsed_time(e1)
     f = c.objective()
     c.close()
-    out = {"order": order, "value": steps / (ms / 1000.0), "unit": "sweeps/s", "ms_per_sweep": ms / steps,
+    out = {"order": order, "gemm": "bf16x9 emulation" if flags & did.DID_FLAG_GEMM_BF16X9 else "float32 SIMT",
+           "value": steps / (ms / 1000.0), "unit": "sweeps/s", "ms_per_sweep": ms / steps,
            "objective_after": f, "sweeps": warmup + steps,
            "sweep_ms": (i1["sweep_kernel_ms"] - i0["sweep_kernel_ms"]) / steps}
     if order == "did_batched":
-        fl = batched_flops(M, N, K)
-        out["roofline"] = {"bound": "alu", "achieved": fl / (out["sweep_ms"] / 1e3) / 1e12,
-                           "peak": FP32_SIMT_TFLOPS, "unit": "TFLOP/s",
-                           "frac": fl / (out["sweep_ms"] / 1e3) / 1e12 / FP32_SIMT_TFLOPS,
-                           "flops_per_sweep": fl, "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
-                           "note": "whole sweep (cuBLAS SGEMMs + solve/update/norm kernels)"}
+        out["roofline"] = batched_roofline(M, N, K, out["sweep_ms"], bool(flags & did.DID_FLAG_GEMM_BF16X9))
     return out
+
+
+def batched_roofline(M, N, K, ms_per_sweep, bf16x9):
+    """Whole-sweep roofline of the batched order: float32 SIMT FMA peak for the
+    pedantic GEMMs; for the BF16x9 emulation, nine bfloat16 products per float32
+    product against the measured bfloat16 tensor peak (sustained)."""
+    fl = batched_flops(M, N, K)
+    tf = fl / (ms_per_sweep / 1e3) / 1e12
+    if not bf16x9:
+        return {"bound": "alu", "achieved": tf, "peak": FP32_SIMT_TFLOPS, "unit": "TFLOP/s",
+                "frac": tf / FP32_SIMT_TFLOPS, "flops_per_sweep": fl,
+                "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                "note": "whole sweep (cuBLAS SGEMMs + solve/update/norm kernels)"}
+    peak, kind = 1700.0, "fallback"
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            peak, kind = float(json.load(f)["bf16_tflops_sustained"]), "measured (sustained)"
+    return {"bound": "tensor", "achieved": 9 * tf, "peak": peak, "unit": "TFLOP/s (bf16 products)",
+            "frac": 9 * tf / peak, "flops_per_sweep": fl, "peak_kind": kind,
+            "note": "whole sweep; float32 flops x 9 bfloat16 products of the BF16x9 emulation"}
 
 
 def dist_env():
@@ -292,6 +309,8 @@ def main():
     ap.add_argument("--order", default="interleaved", choices=sorted(ORDERS),
                     help="block order of the main line: per-k interleaved (Section 4.1), per-k C-first "
                          "(Algorithm 2), or the batched form of Algorithm 3")
+    ap.add_argument("--gemm", default="pedantic", choices=["pedantic", "bf16x9"],
+                    help="GEMMs of the batched order: float32 SIMT or cuBLAS BF16x9 emulation")
     ap.add_argument("--no-orders", action="store_true",
                     help="skip the C-first and batched Algorithm 3 measurements on the same workload")
     ap.add_argument("--phases", action="store_true",
@@ -353,9 +372,11 @@ def main():
 
     if args.order == "did_batched" and prec != did.DID_FP32:
         ap.error("the batched order runs in float32 only")
+    flags = did.DID_FLAG_PHASE_TIMES if args.phases else 0
+    if args.order == "did_batched" and args.gemm == "bf16x9":
+        flags |= did.DID_FLAG_GEMM_BF16X9
     ctx = did.Context(X, M, N, K, seed=seed, precision=prec, order=ORDERS[args.order],
-                      refresh_every=w["refresh_every"], init_scale=w["init_scale"], stream=stream,
-                      flags=did.DID_FLAG_PHASE_TIMES if args.phases else 0)
+                      refresh_every=w["refresh_every"], init_scale=w["init_scale"], stream=stream, flags=flags)
     for _ in range(args.warmup):
         ctx.sweep(1)
     info0 = ctx.info()
@@ -448,12 +469,12 @@ def main():
 
     orders = None
     if not args.no_orders and prec == did.DID_FP32 and args.order == "interleaved":
-        orders = [order_bench(did, X, M, N, K, w, seed, stream, o, args.steps, args.warmup)
-                  for o in ("did", "did_batched")]
+        orders = [order_bench(did, X, M, N, K, w, seed, stream, o, args.steps, args.warmup, f)
+                  for o, f in (("did", 0), ("did_batched", 0), ("did_batched", did.DID_FLAG_GEMM_BF16X9))]
         for o in orders:
             o["ratio_vs_main"] = o["value"] / value
         # the batched form runs 4 of the library's kernels per sweep next to cuBLAS SGEMMs
-        gpu_launches += args.steps + 4 * args.steps
+        gpu_launches += args.steps + 2 * 4 * args.steps
 
     e2e = None
     if not args.no_e2e:
@@ -494,12 +515,8 @@ def main():
         cpu = cpu_baseline(args.workload)
 
     if args.order == "did_batched":
-        fl = batched_flops(M, N, K) * args.steps
-        roofline = {"bound": "alu", "achieved": fl / (kms / 1e3) / 1e12, "peak": FP32_SIMT_TFLOPS,
-                    "unit": "TFLOP/s", "frac": fl / (kms / 1e3) / 1e12 / FP32_SIMT_TFLOPS, "traffic": None,
-                    "kernel": "batched sweep (cuBLAS SGEMMs + solve/update/norm kernels)",
-                    "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
-                    "flops_per_sweep": batched_flops(M, N, K), "kernel_ms_per_sweep": kms / max(1, args.steps)}
+        roofline = batched_roofline(M, N, K, kms / max(1, args.steps), args.gemm == "bf16x9")
+        roofline.update({"traffic": None, "kernel": "batched sweep", "kernel_ms_per_sweep": kms / max(1, args.steps)})
     else:
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                     "frac": achieved / peak, "traffic": traffic if args.order == "interleaved" else None,
@@ -514,7 +531,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == did.DID_FP32 else "bf16-storage/f32",
             "data": "synthetic",
             "config": {"workload": args.workload, "M": M, "N": N, "K": K, "precision": args.precision,
-                       "order": args.order,
+                       "order": args.order, "gemm": args.gemm if args.order == "did_batched" else None,
                        "refresh_every": w["refresh_every"], "init_scale": w["init_scale"],
                        "l2": "inputs larger than L2 (R is %.1f GB)" % (M * N * s_bytes / 1e9),
                        "parallelism": "replicas" if ws > 1 else "single"},

@@ -98,6 +98,11 @@ typedef struct {
 /* did_options.flags: refresh a bfloat16 residual with the float32 SIMT pass
  * instead of the tensor-core BF16x3 pass (for comparisons). */
 #define DID_FLAG_SIMT_REFRESH 2
+/* did_options.flags (DID_ORDER_DID_BATCHED only): run the sweep's float32
+ * GEMMs through cuBLAS's float32 emulation on the bfloat16 tensor cores (each
+ * operand split into three bfloat16 terms, all nine products accumulated in
+ * float32) instead of pedantic float32 SIMT arithmetic. */
+#define DID_FLAG_GEMM_BF16X9 4
 
 typedef struct {
     int64_t M, N;

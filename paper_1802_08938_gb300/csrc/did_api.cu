@@ -469,7 +469,7 @@ static did_status create_impl(did_ctx* c, const float* X, uint64_t seed) {
   if (c->opt.order == DID_ORDER_DID_BATCHED) {
     st = dev_alloc(c, &p, did::batched_workspace_bytes(c->ld, N, K));
     if (st != DID_OK) return st;
-    c->batched = did::batched_create(p, c->ld, N, K, c->stream);
+    c->batched = did::batched_create(p, c->ld, N, K, (c->opt.flags & DID_FLAG_GEMM_BF16X9) != 0, c->stream);
     if (!c->batched) return fail(c, DID_ECUDA, "cuBLAS handle creation failed");
   }
   st = host_alloc(c, &p, sizeof(Ctrl));
@@ -534,7 +534,7 @@ did_status did_create_ex(const float* X, int64_t M, int64_t N, int32_t K, uint64
       (o.order != DID_ORDER_INTERLEAVED && o.order != DID_ORDER_DID && o.order != DID_ORDER_DID_BATCHED) ||
       (o.order == DID_ORDER_DID_BATCHED && (o.precision != DID_FP32 || !did::batched_supported(K))) ||
       (o.stop != DID_STOP_RELCHANGE && o.stop != DID_STOP_PAPER_EPS) || o.refresh_every < 0 ||
-      o.debug_barrier_extra < 0 || (o.flags & ~(DID_FLAG_PHASE_TIMES | DID_FLAG_SIMT_REFRESH)))
+      o.debug_barrier_extra < 0 || (o.flags & ~(DID_FLAG_PHASE_TIMES | DID_FLAG_SIMT_REFRESH | DID_FLAG_GEMM_BF16X9)))
     return DID_EINVAL;
   did_ctx* c = new did_ctx();
   c->M = M;

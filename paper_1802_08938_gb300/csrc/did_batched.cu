@@ -197,6 +197,7 @@ __global__ void objective_kernel(const double* part_n, int nn, const double* par
 
 struct BatchedState {
   cublasHandle_t blas = nullptr;
+  cublasComputeType_t compute = CUBLAS_COMPUTE_32F_PEDANTIC;
   float *g = nullptr, *Z = nullptr, *W = nullptr, *V = nullptr, *YY = nullptr;
   double *part_c = nullptr, *part_b = nullptr, *part_n = nullptr, *state = nullptr;
   int nc = 0, nb = 0, nn = 0;
@@ -204,6 +205,13 @@ struct BatchedState {
 };
 
 bool batched_supported(int K) { return K >= 1 && K <= kMaxK; }
+
+// Column-major float32 GEMM C = alpha op(A) op(B) + beta C in the state's compute type.
+static bool gemm(BatchedState* b, cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k, float alpha,
+                 const float* A, int lda, const float* B, int ldb, float beta, float* C, int ldc) {
+  return cublasGemmEx(b->blas, ta, tb, m, n, k, &alpha, A, CUDA_R_32F, lda, B, CUDA_R_32F, ldb, &beta, C, CUDA_R_32F,
+                      ldc, b->compute, CUBLAS_GEMM_DEFAULT) == CUBLAS_STATUS_SUCCESS;
+}
 
 size_t batched_workspace_bytes(int ld, int64_t N, int K) {
   const int nc = (int)((N + kSolveThreads - 1) / kSolveThreads);
@@ -214,14 +222,22 @@ size_t batched_workspace_bytes(int ld, int64_t N, int K) {
 
 static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
-BatchedState* batched_create(void* ws, int ld, int64_t N, int K, cudaStream_t s) {
+BatchedState* batched_create(void* ws, int ld, int64_t N, int K, bool bf16x9, cudaStream_t s) {
   BatchedState* b = new BatchedState();
   if (cublasCreate(&b->blas) != CUBLAS_STATUS_SUCCESS) {
     delete b;
     return nullptr;
   }
   cublasSetStream(b->blas, s);
-  cublasSetMathMode(b->blas, CUBLAS_PEDANTIC_MATH);   // float32 products, no reduced-precision shortcuts
+  if (bf16x9) {
+    // float32 emulated on the bfloat16 tensor cores, used for every shape
+    b->compute = CUBLAS_COMPUTE_32F_EMULATED_16BFX9;
+    cublasSetMathMode(b->blas, CUBLAS_FP32_EMULATED_BF16X9_MATH);
+    cublasSetEmulationStrategy(b->blas, CUBLAS_EMULATION_STRATEGY_EAGER);
+  } else {
+    b->compute = CUBLAS_COMPUTE_32F_PEDANTIC;
+    cublasSetMathMode(b->blas, CUBLAS_PEDANTIC_MATH);   // float32 products, no reduced-precision shortcuts
+  }
   b->nc = (int)((N + kSolveThreads - 1) / kSolveThreads);
   b->nb = (ld + kBThreads - 1) / kBThreads;
   unsigned char* p = static_cast<unsigned char*>(ws);
@@ -262,9 +278,7 @@ cudaError_t batched_reset(BatchedState* b, float* Y, int ld, int K, double e2, c
   if (e != cudaSuccess) return e;
   e = cudaMemcpyAsync(b->state, &e2, sizeof(double), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return e;
-  const float one = 1.f, zero = 0.f;
-  if (cublasSgemm(b->blas, CUBLAS_OP_T, CUBLAS_OP_N, 2 * K, 2 * K, ld, &one, Y, ld, Y, ld, &zero, b->YY, 2 * K) !=
-      CUBLAS_STATUS_SUCCESS)
+  if (!gemm(b, CUBLAS_OP_T, CUBLAS_OP_N, 2 * K, 2 * K, ld, 1.f, Y, ld, Y, ld, 0.f, b->YY, 2 * K))
     return cudaErrorUnknown;
   b->d_pending = false;
   // the host value e2 must stay valid until the copy ran
@@ -274,17 +288,14 @@ cudaError_t batched_reset(BatchedState* b, float* Y, int ld, int K, double e2, c
 // One batched sweep.  R (ld x N), Y = [D | B] (ld x 2K), C (K x N row-major).
 cudaError_t batched_sweep(BatchedState* b, float* R, float* Y, float* C, int ld, int64_t N, int K,
                           unsigned long long* degen, double* trace_out, cudaStream_t s) {
-  const float one = 1.f, zero = 0.f, mone = -1.f;
   const int K2 = 2 * K;
   float* Bm = Y + (size_t)K * ld;
   // g = B^T R_s  (K x N) ;  g -= (B^T D) C
-  if (cublasSgemm(b->blas, CUBLAS_OP_T, CUBLAS_OP_N, K, (int)N, ld, &one, Bm, ld, R, ld, &zero, b->g, K) !=
-      CUBLAS_STATUS_SUCCESS)
+  if (!gemm(b, CUBLAS_OP_T, CUBLAS_OP_N, K, (int)N, ld, 1.f, Bm, ld, R, ld, 0.f, b->g, K))
     return cudaErrorUnknown;
   if (b->d_pending) {
     // H = (B^T D) is the block rows K..2K-1, columns 0..K-1 of Y^T Y.
-    if (cublasSgemm(b->blas, CUBLAS_OP_N, CUBLAS_OP_T, K, (int)N, K, &mone, b->YY + K, K2, C, (int)N, &one, b->g,
-                    K) != CUBLAS_STATUS_SUCCESS)
+    if (!gemm(b, CUBLAS_OP_N, CUBLAS_OP_T, K, (int)N, K, -1.f, b->YY + K, K2, C, (int)N, 1.f, b->g, K))
       return cudaErrorUnknown;
   }
   solve_c_kernel<<<b->nc, kSolveThreads, (size_t)K * K * 4, s>>>(b->g, C, b->YY, b->Z, b->part_c, degen, K, N);
@@ -292,12 +303,10 @@ cudaError_t batched_sweep(BatchedState* b, float* R, float* Y, float* C, int ld,
   if (e != cudaSuccess) return e;
   // R_s := R_s - [D B] [C_old; dl]  (the D half only while a correction is pending)
   if (b->d_pending) {
-    if (cublasSgemm(b->blas, CUBLAS_OP_N, CUBLAS_OP_N, ld, (int)N, K2, &mone, Y, ld, b->Z, K2, &one, R, ld) !=
-        CUBLAS_STATUS_SUCCESS)
+    if (!gemm(b, CUBLAS_OP_N, CUBLAS_OP_N, ld, (int)N, K2, -1.f, Y, ld, b->Z, K2, 1.f, R, ld))
       return cudaErrorUnknown;
   } else {
-    if (cublasSgemm(b->blas, CUBLAS_OP_N, CUBLAS_OP_N, ld, (int)N, K, &mone, Bm, ld, b->Z + K, K2, &one, R, ld) !=
-        CUBLAS_STATUS_SUCCESS)
+    if (!gemm(b, CUBLAS_OP_N, CUBLAS_OP_N, ld, (int)N, K, -1.f, Bm, ld, b->Z + K, K2, 1.f, R, ld))
       return cudaErrorUnknown;
   }
   // ||E'||^2 of the updated residual (ld*N is a multiple of 4: ld is)
@@ -305,18 +314,15 @@ cudaError_t batched_sweep(BatchedState* b, float* R, float* Y, float* C, int ld,
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // W = R C'^T (ld x K), V = C' C'^T (K x K): C' row-major K x N is column-major N x K.
-  if (cublasSgemm(b->blas, CUBLAS_OP_N, CUBLAS_OP_N, ld, K, (int)N, &one, R, ld, C, (int)N, &zero, b->W, ld) !=
-      CUBLAS_STATUS_SUCCESS)
+  if (!gemm(b, CUBLAS_OP_N, CUBLAS_OP_N, ld, K, (int)N, 1.f, R, ld, C, (int)N, 0.f, b->W, ld))
     return cudaErrorUnknown;
-  if (cublasSgemm(b->blas, CUBLAS_OP_T, CUBLAS_OP_N, K, K, (int)N, &one, C, (int)N, C, (int)N, &zero, b->V, K) !=
-      CUBLAS_STATUS_SUCCESS)
+  if (!gemm(b, CUBLAS_OP_T, CUBLAS_OP_N, K, K, (int)N, 1.f, C, (int)N, C, (int)N, 0.f, b->V, K))
     return cudaErrorUnknown;
   update_b_kernel<<<b->nb, kBThreads, (size_t)K * K * 4, s>>>(b->W, b->V, Y, b->part_b, degen, K, ld);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // Y^T Y gives B^T B, B^T D and D^T D for the objective and the next sweep.
-  if (cublasSgemm(b->blas, CUBLAS_OP_T, CUBLAS_OP_N, K2, K2, ld, &one, Y, ld, Y, ld, &zero, b->YY, K2) !=
-      CUBLAS_STATUS_SUCCESS)
+  if (!gemm(b, CUBLAS_OP_T, CUBLAS_OP_N, K2, K2, ld, 1.f, Y, ld, Y, ld, 0.f, b->YY, K2))
     return cudaErrorUnknown;
   objective_kernel<<<1, 256, 0, s>>>(b->part_n, b->nn, b->part_b, b->nb, b->YY, b->V, K, b->state, trace_out);
   e = cudaGetLastError();
@@ -328,14 +334,11 @@ cudaError_t batched_sweep(BatchedState* b, float* R, float* Y, float* C, int ld,
 cudaError_t batched_materialize(BatchedState* b, float* R, float* Y, const float* C, int ld, int64_t N, int K,
                                 cudaStream_t s) {
   if (!b->d_pending) return cudaSuccess;
-  const float one = 1.f, mone = -1.f, zero = 0.f;
-  if (cublasSgemm(b->blas, CUBLAS_OP_N, CUBLAS_OP_T, ld, (int)N, K, &mone, Y, ld, C, (int)N, &one, R, ld) !=
-      CUBLAS_STATUS_SUCCESS)
+  if (!gemm(b, CUBLAS_OP_N, CUBLAS_OP_T, ld, (int)N, K, -1.f, Y, ld, C, (int)N, 1.f, R, ld))
     return cudaErrorUnknown;
   cudaError_t e = cudaMemsetAsync(Y, 0, (size_t)ld * K * 4, s);
   if (e != cudaSuccess) return e;
-  if (cublasSgemm(b->blas, CUBLAS_OP_T, CUBLAS_OP_N, 2 * K, 2 * K, ld, &one, Y, ld, Y, ld, &zero, b->YY, 2 * K) !=
-      CUBLAS_STATUS_SUCCESS)
+  if (!gemm(b, CUBLAS_OP_T, CUBLAS_OP_N, 2 * K, 2 * K, ld, 1.f, Y, ld, Y, ld, 0.f, b->YY, 2 * K))
     return cudaErrorUnknown;
   b->d_pending = false;
   return cudaSuccess;

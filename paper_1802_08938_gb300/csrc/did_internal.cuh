@@ -356,7 +356,7 @@ cudaError_t launch_refresh_tc(const float* X, void* R, const float* B, const flo
 struct BatchedState;
 bool batched_supported(int K);
 size_t batched_workspace_bytes(int ld, int64_t N, int K);
-BatchedState* batched_create(void* ws, int ld, int64_t N, int K, cudaStream_t s);
+BatchedState* batched_create(void* ws, int ld, int64_t N, int K, bool bf16x9, cudaStream_t s);
 void batched_destroy(BatchedState* b);
 cudaError_t batched_reset(BatchedState* b, float* Y, int ld, int K, double e2, cudaStream_t s);
 cudaError_t batched_sweep(BatchedState* b, float* R, float* Y, float* C, int ld, int64_t N, int K,

@@ -36,18 +36,20 @@ def run(did, X, B0, C0, sweeps, order, **kw):
         return B, C, ctx.trace(), ctx.residual(), ctx.objective()
 
 
+@pytest.mark.parametrize("gemm", ["pedantic", "bf16x9"])
 @pytest.mark.parametrize("M,N,K", [(200, 1000, 10), (37, 53, 3), (784, 700, 16), (2001, 311, 5), (300, 5000, 64),
                                    (129, 257, 128)])
-def test_batched_matches_algorithm3(did, M, N, K):
+def test_batched_matches_algorithm3(did, M, N, K, gemm):
     X, _, _ = W.planted(M, N, K, seed=M + 5 * N, sigma=0.01)
     B0, C0 = W.init_factors(M, N, K, 6)
     sweeps = 20
     ref = O.factor(X, B0, C0, order="did", max_iter=sweeps, stop="none")
-    B, C, t, R, fx = run(did, X, B0, C0, sweeps, did.DID_ORDER_DID_BATCHED)
+    flags = did.DID_FLAG_GEMM_BF16X9 if gemm == "bf16x9" else 0
+    B, C, t, R, fx = run(did, X, B0, C0, sweeps, did.DID_ORDER_DID_BATCHED, flags=flags)
     eB, eC = rel_fro(B, ref["B"]), rel_fro(C, ref["C"])
     eF = abs(t[-1] - ref["trace"][-1]) / ref["trace"][-1]
-    print("batched M=%d N=%d K=%d: relB %.3g relC %.3g relf %.3g (exact f %.3g)" % (
-        M, N, K, eB, eC, eF, abs(fx - ref["trace"][-1]) / ref["trace"][-1]))
+    print("batched %s M=%d N=%d K=%d: relB %.3g relC %.3g relf %.3g (exact f %.3g)" % (
+        gemm, M, N, K, eB, eC, eF, abs(fx - ref["trace"][-1]) / ref["trace"][-1]))
     assert eB <= 1e-4 and eC <= 1e-4 and eF <= 1e-5
     assert B.min() >= 0 and C.min() >= 0
     Rd = X.astype(np.float64) - B.astype(np.float64) @ C.astype(np.float64)
