@@ -216,11 +216,12 @@ def batched_flops(M, N, K):
     return 8.0 * K * M * N + 2.0 * K * K * N * 2 + 2.0 * (2 * K) ** 2 * M + 2.0 * K * K * (N + M)
 
 
-def order_bench(did, X, M, N, K, w, seed, stream, order, steps, warmup, flags=0):
+def order_bench(did, X, M, N, K, w, seed, stream, order, steps, warmup, flags=0, inner=(1, 1)):
     """Sweeps/s of one block order on the same workload, seed and start."""
     import torch
     c = did.Context(X, M, N, K, seed=seed, precision=did.DID_FP32, order=ORDERS[order],
-                    refresh_every=w["refresh_every"], init_scale=w["init_scale"], stream=stream, flags=flags)
+                    refresh_every=w["refresh_every"], init_scale=w["init_scale"], stream=stream, flags=flags,
+                    inner_c=inner[0], inner_b=inner[1])
     for _ in range(warmup):
         c.sweep(1)
     i0 = c.info()
@@ -235,8 +236,10 @@ def order_bench(did, X, M, N, K, w, seed, stream, order, steps, warmup, flags=0)
     i1 = c.info()
     ms = e0.elapsed_time(e1)
     f = c.objective()
+    trace = c.trace()
     c.close()
     out = {"order": order, "gemm": "bf16x9 emulation" if flags & did.DID_FLAG_GEMM_BF16X9 else "float32 SIMT",
+           "inner": list(inner), "trace": [float(v) for v in trace],
            "value": steps / (ms / 1000.0), "unit": "sweeps/s", "ms_per_sweep": ms / steps,
            "objective_after": f, "sweeps": warmup + steps,
            "sweep_ms": (i1["sweep_kernel_ms"] - i0["sweep_kernel_ms"]) / steps}
@@ -469,12 +472,19 @@ def main():
 
     orders = None
     if not args.no_orders and prec == did.DID_FP32 and args.order == "interleaved":
-        orders = [order_bench(did, X, M, N, K, w, seed, stream, o, args.steps, args.warmup, f)
-                  for o, f in (("did", 0), ("did_batched", 0), ("did_batched", did.DID_FLAG_GEMM_BF16X9))]
+        x9 = did.DID_FLAG_GEMM_BF16X9
+        orders = [order_bench(did, X, M, N, K, w, seed, stream, o, args.steps, args.warmup, f, r)
+                  for o, f, r in (("did", 0, (1, 1)), ("did_batched", 0, (1, 1)), ("did_batched", x9, (1, 1)),
+                                  ("did_batched", x9, (2, 2)), ("did_batched", x9, (4, 4)))]
+        # inner repeats: sweeps (and time) to reach the objective that plain batched sweeps reach
+        target = orders[2]["trace"][-1]
         for o in orders:
             o["ratio_vs_main"] = o["value"] / value
+            hit = [i for i, v in enumerate(o.pop("trace")) if v <= target]
+            o["sweeps_to_plain_final"] = hit[0] if hit else None
+            o["ms_to_plain_final"] = hit[0] * o["ms_per_sweep"] if hit else None
         # the batched form runs 4 of the library's kernels per sweep next to cuBLAS SGEMMs
-        gpu_launches += args.steps + 2 * 4 * args.steps
+        gpu_launches += args.steps + 4 * 4 * args.steps
 
     e2e = None
     if not args.no_e2e:

@@ -88,6 +88,14 @@ typedef struct {
     uint64_t timeout_ns;    /* limit of every device-side grid wait; 0 = 4 s */
     int32_t debug_barrier_extra; /* test hook: arrivals a grid wait expects beyond the grid (0 in use) */
     int32_t flags;          /* DID_FLAG_* bits */
+    /* Inner repeats per sweep (DID_ORDER_DID_BATCHED only; 0 means 1): the C
+     * step runs inner_c times, then the B step inner_b times, each repeat the
+     * same exact block minimisation on the current residual.  This is the
+     * acceleration the paper leaves to future work (Section 6), after Gillis &
+     * Glineur's accelerated HALS; a repeat costs O(K^2) per column (C) or per
+     * row (B) and no pass over R.  At most 64 each; otherwise DID_EINVAL. */
+    int32_t inner_c;
+    int32_t inner_b;
 } did_options;
 
 /* did_options.flags: record %globaltimer stamps of the sweep phases (CTA 0):

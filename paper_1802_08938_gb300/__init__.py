@@ -47,6 +47,8 @@ class did_options(ctypes.Structure):
         ("timeout_ns", ctypes.c_uint64),
         ("debug_barrier_extra", ctypes.c_int32),
         ("flags", ctypes.c_int32),
+        ("inner_c", ctypes.c_int32),
+        ("inner_b", ctypes.c_int32),
     ]
 
 
@@ -329,13 +331,15 @@ class Context:
 
     def __init__(self, X, M, N, K, seed=0, precision=DID_FP32, order=DID_ORDER_INTERLEAVED,
                  refresh_every=0, stop=DID_STOP_RELCHANGE, init_scale=False, grid_ctas=0,
-                 B_init=None, C_init=None, stream=None, timeout_ns=0, debug_barrier_extra=0, flags=0):
+                 B_init=None, C_init=None, stream=None, timeout_ns=0, debug_barrier_extra=0, flags=0,
+                 inner_c=1, inner_b=1):
         o = default_options()
         o.precision, o.order, o.refresh_every, o.stop = precision, order, refresh_every, stop
         o.init_scale, o.grid_ctas = int(bool(init_scale)), grid_ctas
         o.B_init, o.C_init = _ptr(B_init), _ptr(C_init)
         o.stream = _stream_of(stream)
         o.timeout_ns, o.debug_barrier_extra, o.flags = timeout_ns, debug_barrier_extra, flags
+        o.inner_c, o.inner_b = inner_c, inner_b
         self.M, self.N, self.K = int(M), int(N), int(K)
         self._keep = (X, B_init, C_init)
         self.h = did_create(X, self.M, self.N, self.K, seed, o)

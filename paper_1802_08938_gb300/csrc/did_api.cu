@@ -339,8 +339,8 @@ did_status run_batched(did_ctx* c, int64_t max_sweeps, int stop_rule, double tol
     const int n = stop_rule ? 1 : chunk;     // with a stopping rule: one sweep per check
     DID_CUDA(c, cudaEventRecord(c->ev0, c->stream));
     for (int s = 0; s < n; ++s)
-      DID_CUDA(c, did::batched_sweep(c->batched, (float*)c->R, c->Y, c->C, c->ld, c->N, c->K, c->degen,
-                                     c->trace_dev + s, c->stream));
+      DID_CUDA(c, did::batched_sweep(c->batched, (float*)c->R, c->Y, c->C, c->ld, c->N, c->K, c->opt.inner_c,
+                                     c->opt.inner_b, c->degen, c->trace_dev + s, c->stream));
     DID_CUDA(c, cudaEventRecord(c->ev1, c->stream));
     DID_CUDA(c, cudaMemcpyAsync(c->trace_host, c->trace_dev, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
     DID_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -395,6 +395,8 @@ void did_default_options(did_options* opt) {
   opt->refresh_every = 0;
   opt->stop = DID_STOP_RELCHANGE;
   opt->timeout_ns = 0;
+  opt->inner_c = 1;
+  opt->inner_b = 1;
 }
 
 const char* did_status_string(did_status s) {
@@ -534,8 +536,12 @@ did_status did_create_ex(const float* X, int64_t M, int64_t N, int32_t K, uint64
       (o.order != DID_ORDER_INTERLEAVED && o.order != DID_ORDER_DID && o.order != DID_ORDER_DID_BATCHED) ||
       (o.order == DID_ORDER_DID_BATCHED && (o.precision != DID_FP32 || !did::batched_supported(K))) ||
       (o.stop != DID_STOP_RELCHANGE && o.stop != DID_STOP_PAPER_EPS) || o.refresh_every < 0 ||
-      o.debug_barrier_extra < 0 || (o.flags & ~(DID_FLAG_PHASE_TIMES | DID_FLAG_SIMT_REFRESH | DID_FLAG_GEMM_BF16X9)))
+      o.debug_barrier_extra < 0 || (o.flags & ~(DID_FLAG_PHASE_TIMES | DID_FLAG_SIMT_REFRESH | DID_FLAG_GEMM_BF16X9)) ||
+      o.inner_c < 0 || o.inner_c > 64 || o.inner_b < 0 || o.inner_b > 64 ||
+      (o.order != DID_ORDER_DID_BATCHED && (o.inner_c > 1 || o.inner_b > 1)))
     return DID_EINVAL;
+  if (o.inner_c == 0) o.inner_c = 1;
+  if (o.inner_b == 0) o.inner_b = 1;
   did_ctx* c = new did_ctx();
   c->M = M;
   c->N = N;

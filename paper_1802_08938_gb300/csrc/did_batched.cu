@@ -14,6 +14,11 @@
 //            per row m, i = 1..K (Section 4.2 update of b_i):
 //              b_i' = [b_i + (w_i - sum_{k<i} V_ik db_k) / V_ii]_+ ,  db_i = b_i' - b_i
 //            D := db (applied lazily by the next C step)
+// Inner repeats (the acceleration named as future work in Section 6, after
+// Gillis & Glineur's accelerated HALS) run the per-column pass reps_c times
+// and the per-row pass reps_b times: with dl and db accumulated over all
+// repeats, the residual after them is still E - B dl (C step) and E' - db C'
+// (B step), so a repeat needs g, G, W and V only -- no pass over R.
 // The objective of the sweep: ||E'||^2 = ||R_s||^2 right after the rank-2K
 // update (a deterministic norm pass), then the B step's change from an exact
 // identity in float64:
@@ -23,8 +28,9 @@
 // the float32 rounding of g over the sweeps).  A dense refresh re-anchors
 // R_s = X - B C and D = 0.
 //
-// The large products are plain GEMMs and use cuBLAS SGEMM (float32); the two
-// sequential solves, the bookkeeping and the objective are the kernels below.
+// The large products are plain GEMMs and use cuBLAS (float32 SGEMM, or its
+// BF16x9 emulation); the sequential solves, the norm and the objective are
+// the kernels below.
 #include "did_internal.cuh"
 
 #include <cublas_v2.h>
@@ -38,13 +44,15 @@ constexpr int kMaxK = 128;
 constexpr int kSolveThreads = 128;
 constexpr int kBThreads = 128;
 
-// Per column: the K successive c updates from g = B^T E and G = B^T B.
-// Z (2K x N, column-major, ld 2K) receives [C_old; dl].  Block partials of
-// sum g.dl and sum dl^T G dl in float64.
+// Per column: reps passes of the K successive c updates, from g = B^T E and
+// G = B^T B.  With dl the change of the column so far (all repeats),
+//   t_i = g_ij - sum_l G_il dl_l ;  c_ij := [c_ij + t_i / G_ii]_+
+// (in the first pass dl_l = 0 for l >= i, so the sum runs over l < i).
+// Z (2K x N, column-major, ld 2K) receives [C_old; dl].
 __global__ void __launch_bounds__(kSolveThreads) solve_c_kernel(const float* __restrict__ g, float* C,
                                                                 const float* __restrict__ YY, float* Z,
-                                                                double* part, unsigned long long* degen, int K,
-                                                                int64_t N) {
+                                                                unsigned long long* degen, int K, int64_t N,
+                                                                int reps) {
   extern __shared__ float Gs[];          // K x K, G_il at Gs[i*K + l]
   const int K2 = 2 * K;
   for (int idx = threadIdx.x; idx < K * K; idx += blockDim.x) {
@@ -52,53 +60,44 @@ __global__ void __launch_bounds__(kSolveThreads) solve_c_kernel(const float* __r
     Gs[idx] = YY[(size_t)(K + i) + (size_t)(K + l) * K2];   // (B^T B)_il from Y^T Y
   }
   __syncthreads();
-  __shared__ double red[2][kSolveThreads / 32];
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  double gd = 0.0, dgd = 0.0;
-  if (j < N) {
-    float dl[kMaxK];
-    const float* gj = g + (size_t)j * K;
+  if (j >= N) return;
+  float c0[kMaxK], cur[kMaxK], dl[kMaxK];
+  const float* gj = g + (size_t)j * K;
+  for (int i = 0; i < K; ++i) {
+    c0[i] = cur[i] = C[(size_t)i * N + j];
+    dl[i] = 0.f;
+  }
+  for (int r = 0; r < reps; ++r) {
     for (int i = 0; i < K; ++i) {
+      const int lend = r == 0 ? i : K;
       float sl = 0.f;
-      for (int l = 0; l < i; ++l) sl = fmaf(Gs[i * K + l], dl[l], sl);
-      const float gi = gj[i];
-      const float c_old = C[(size_t)i * N + j];
+      for (int l = 0; l < lend; ++l) sl = fmaf(Gs[i * K + l], dl[l], sl);
       const float gii = Gs[i * K + i];
-      float c_new = c_old;
       if (gii > 0.f) {
-        const float t = c_old + (gi - sl) / gii;
-        c_new = t > 0.f ? t : 0.f;
+        const float t = cur[i] + (gj[i] - sl) / gii;
+        cur[i] = t > 0.f ? t : 0.f;
+        dl[i] = cur[i] - c0[i];
       } else if (j == 0) {
         atomicAdd(degen, 1ull);
       }
-      const float d = c_new - c_old;
-      dl[i] = d;
-      C[(size_t)i * N + j] = c_new;
-      Z[(size_t)i + (size_t)j * K2] = c_old;
-      Z[(size_t)(K + i) + (size_t)j * K2] = d;
-      gd += (double)gi * (double)d;
-      dgd += (double)d * (double)d * (double)gii + 2.0 * (double)d * (double)sl;
     }
   }
-  gd = warp_sum_f64(gd);
-  dgd = warp_sum_f64(dgd);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) { red[0][w] = gd; red[1][w] = dgd; }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = 0.0, b = 0.0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { a += red[0][i]; b += red[1][i]; }
-    part[2 * blockIdx.x] = a;
-    part[2 * blockIdx.x + 1] = b;
+  for (int i = 0; i < K; ++i) {
+    C[(size_t)i * N + j] = cur[i];
+    Z[(size_t)i + (size_t)j * K2] = c0[i];
+    Z[(size_t)(K + i) + (size_t)j * K2] = dl[i];
   }
 }
 
-// Per row m: the K successive b updates from W = E' C'^T and V = C' C'^T.
+// Per row m: reps passes of the K successive b updates from W = E' C'^T and
+// V = C' C'^T (the delta-b rule of Section 4.2, over all repeats):
+//   b_i := [b_i + (w_i - sum_k V_ik db_k) / V_ii]_+ ,  db = b - b_old.
 // Y (ld x 2K, column-major) holds [D | B]; B is replaced by B', D by db.
 // Block partials of sum_i db_i[m] W[m,i] in float64.
 __global__ void __launch_bounds__(kBThreads) update_b_kernel(const float* __restrict__ W, const float* __restrict__ V,
                                                              float* Y, double* part, unsigned long long* degen,
-                                                             int K, int ld) {
+                                                             int K, int ld, int reps) {
   extern __shared__ float Vs[];          // K x K, V_ik at Vs[i*K + k] (column-major V is symmetric)
   for (int idx = threadIdx.x; idx < K * K; idx += blockDim.x) Vs[idx] = V[idx];
   __syncthreads();
@@ -106,26 +105,30 @@ __global__ void __launch_bounds__(kBThreads) update_b_kernel(const float* __rest
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   double dw = 0.0;
   if (m < ld) {
-    float db[kMaxK];
+    float b0[kMaxK], cur[kMaxK], db[kMaxK];
     for (int i = 0; i < K; ++i) {
-      float s = 0.f;
-      for (int k = 0; k < i; ++k) s = fmaf(Vs[i * K + k], db[k], s);
-      const float wi = W[(size_t)m + (size_t)i * ld];
-      float* bp = Y + (size_t)m + (size_t)(K + i) * ld;
-      const float b_old = *bp;
-      const float vii = Vs[i * K + i];
-      float b_new = b_old;
-      if (vii > 0.f) {
-        const float t = b_old + (wi - s) / vii;
-        b_new = t > 0.f ? t : 0.f;
-      } else if (m == 0) {
-        atomicAdd(degen, 1ull);
+      b0[i] = cur[i] = Y[(size_t)m + (size_t)(K + i) * ld];
+      db[i] = 0.f;
+    }
+    for (int r = 0; r < reps; ++r) {
+      for (int i = 0; i < K; ++i) {
+        const int kend = r == 0 ? i : K;
+        float s = 0.f;
+        for (int k = 0; k < kend; ++k) s = fmaf(Vs[i * K + k], db[k], s);
+        const float vii = Vs[i * K + i];
+        if (vii > 0.f) {
+          const float t = cur[i] + (W[(size_t)m + (size_t)i * ld] - s) / vii;
+          cur[i] = t > 0.f ? t : 0.f;
+          db[i] = cur[i] - b0[i];
+        } else if (m == 0) {
+          atomicAdd(degen, 1ull);
+        }
       }
-      const float d = b_new - b_old;
-      db[i] = d;
-      *bp = b_new;
-      Y[(size_t)m + (size_t)i * ld] = d;
-      dw += (double)d * (double)wi;
+    }
+    for (int i = 0; i < K; ++i) {
+      Y[(size_t)m + (size_t)(K + i) * ld] = cur[i];
+      Y[(size_t)m + (size_t)i * ld] = db[i];
+      dw += (double)db[i] * (double)W[(size_t)m + (size_t)i * ld];
     }
   }
   dw = warp_sum_f64(dw);
@@ -199,7 +202,7 @@ struct BatchedState {
   cublasHandle_t blas = nullptr;
   cublasComputeType_t compute = CUBLAS_COMPUTE_32F_PEDANTIC;
   float *g = nullptr, *Z = nullptr, *W = nullptr, *V = nullptr, *YY = nullptr;
-  double *part_c = nullptr, *part_b = nullptr, *part_n = nullptr, *state = nullptr;
+  double *part_b = nullptr, *part_n = nullptr, *state = nullptr;
   int nc = 0, nb = 0, nn = 0;
   bool d_pending = false;
 };
@@ -214,10 +217,9 @@ static bool gemm(BatchedState* b, cublasOperation_t ta, cublasOperation_t tb, in
 }
 
 size_t batched_workspace_bytes(int ld, int64_t N, int K) {
-  const int nc = (int)((N + kSolveThreads - 1) / kSolveThreads);
   const int nb = (ld + kBThreads - 1) / kBThreads;
   return (size_t)K * N * 4 + (size_t)2 * K * N * 4 + (size_t)ld * K * 4 + (size_t)K * K * 4 + (size_t)4 * K * K * 4 +
-         (size_t)(2 * nc + nb + 2 + 4096) * 8 + 8 * 256;
+         (size_t)(nb + 2 + 4096) * 8 + 8 * 256;
 }
 
 static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -247,7 +249,6 @@ BatchedState* batched_create(void* ws, int ld, int64_t N, int K, bool bf16x9, cu
   b->W = (float*)take((size_t)ld * K * 4);
   b->V = (float*)take((size_t)K * K * 4);
   b->YY = (float*)take((size_t)4 * K * K * 4);
-  b->part_c = (double*)take((size_t)2 * b->nc * 8);
   b->part_b = (double*)take((size_t)b->nb * 8);
   b->part_n = (double*)take((size_t)4096 * 8);
   b->state = (double*)take(2 * 8);
@@ -286,8 +287,8 @@ cudaError_t batched_reset(BatchedState* b, float* Y, int ld, int K, double e2, c
 }
 
 // One batched sweep.  R (ld x N), Y = [D | B] (ld x 2K), C (K x N row-major).
-cudaError_t batched_sweep(BatchedState* b, float* R, float* Y, float* C, int ld, int64_t N, int K,
-                          unsigned long long* degen, double* trace_out, cudaStream_t s) {
+cudaError_t batched_sweep(BatchedState* b, float* R, float* Y, float* C, int ld, int64_t N, int K, int reps_c,
+                          int reps_b, unsigned long long* degen, double* trace_out, cudaStream_t s) {
   const int K2 = 2 * K;
   float* Bm = Y + (size_t)K * ld;
   // g = B^T R_s  (K x N) ;  g -= (B^T D) C
@@ -298,7 +299,7 @@ cudaError_t batched_sweep(BatchedState* b, float* R, float* Y, float* C, int ld,
     if (!gemm(b, CUBLAS_OP_N, CUBLAS_OP_T, K, (int)N, K, -1.f, b->YY + K, K2, C, (int)N, 1.f, b->g, K))
       return cudaErrorUnknown;
   }
-  solve_c_kernel<<<b->nc, kSolveThreads, (size_t)K * K * 4, s>>>(b->g, C, b->YY, b->Z, b->part_c, degen, K, N);
+  solve_c_kernel<<<b->nc, kSolveThreads, (size_t)K * K * 4, s>>>(b->g, C, b->YY, b->Z, degen, K, N, reps_c);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // R_s := R_s - [D B] [C_old; dl]  (the D half only while a correction is pending)
@@ -318,7 +319,7 @@ cudaError_t batched_sweep(BatchedState* b, float* R, float* Y, float* C, int ld,
     return cudaErrorUnknown;
   if (!gemm(b, CUBLAS_OP_T, CUBLAS_OP_N, K, K, (int)N, 1.f, C, (int)N, C, (int)N, 0.f, b->V, K))
     return cudaErrorUnknown;
-  update_b_kernel<<<b->nb, kBThreads, (size_t)K * K * 4, s>>>(b->W, b->V, Y, b->part_b, degen, K, ld);
+  update_b_kernel<<<b->nb, kBThreads, (size_t)K * K * 4, s>>>(b->W, b->V, Y, b->part_b, degen, K, ld, reps_b);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // Y^T Y gives B^T B, B^T D and D^T D for the objective and the next sweep.

@@ -359,7 +359,7 @@ size_t batched_workspace_bytes(int ld, int64_t N, int K);
 BatchedState* batched_create(void* ws, int ld, int64_t N, int K, bool bf16x9, cudaStream_t s);
 void batched_destroy(BatchedState* b);
 cudaError_t batched_reset(BatchedState* b, float* Y, int ld, int K, double e2, cudaStream_t s);
-cudaError_t batched_sweep(BatchedState* b, float* R, float* Y, float* C, int ld, int64_t N, int K,
+cudaError_t batched_sweep(BatchedState* b, float* R, float* Y, float* C, int ld, int64_t N, int K, int reps_c, int reps_b,
                           unsigned long long* degen, double* trace_out, cudaStream_t s);
 cudaError_t batched_materialize(BatchedState* b, float* R, float* Y, const float* C, int ld, int64_t N, int K,
                                 cudaStream_t s);

@@ -65,7 +65,7 @@ def test_options_struct_layout(lib):
     assert o.precision == did.DID_FP32 and o.order == did.DID_ORDER_INTERLEAVED
     assert o.refresh_every == 0 and o.debug_barrier_extra == 0
     # 6 int32 + 3 pointers + uint64 + 2 int32 on an LP64 ABI
-    assert ctypes.sizeof(did.did_options) == 6 * 4 + 3 * 8 + 8 + 2 * 4
+    assert ctypes.sizeof(did.did_options) == 6 * 4 + 3 * 8 + 8 + 4 * 4
 
 
 def test_host_side_argument_checks_need_no_gpu(lib):

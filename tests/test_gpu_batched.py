@@ -93,3 +93,39 @@ def test_batched_rejects_bf16_and_large_k(did):
         did.Context(X, 200, 300, 4, order=did.DID_ORDER_DID_BATCHED, precision=did.DID_BF16R)
     with pytest.raises(did.DIDError):
         did.Context(X, 200, 300, 150, order=did.DID_ORDER_DID_BATCHED)
+
+
+@pytest.mark.parametrize("reps", [(3, 3), (6, 1), (1, 5)])
+@pytest.mark.parametrize("M,N,K", [(200, 1000, 10), (784, 700, 16), (65, 3001, 24)])
+def test_inner_repeats_match_oracle(did, M, N, K, reps):
+    X, _, _ = W.planted(M, N, K, seed=M + N + K, sigma=0.01)
+    B0, C0 = W.init_factors(M, N, K, 8)
+    sweeps = 10
+    ref = O.factor(X, B0, C0, order="did", max_iter=sweeps, stop="none", inner_c=reps[0], inner_b=reps[1])
+    B, C, t, R, fx = run(did, X, B0, C0, sweeps, did.DID_ORDER_DID_BATCHED, inner_c=reps[0], inner_b=reps[1])
+    eB, eC = rel_fro(B, ref["B"]), rel_fro(C, ref["C"])
+    eF = np.max(np.abs(t - ref["trace"]) / ref["trace"])
+    print("repeats %s M=%d N=%d K=%d: relB %.3g relC %.3g max relf %.3g" % (reps, M, N, K, eB, eC, eF))
+    assert eB <= 1e-4 and eC <= 1e-4 and eF <= 1e-5
+    assert np.all(np.diff(t) <= 1e-6 * t[0])
+    assert B.min() >= 0 and C.min() >= 0
+
+
+def test_inner_repeats_lower_the_objective_per_sweep(did):
+    M, N, K = 300, 4000, 12
+    X, _, _ = W.planted(M, N, K, seed=21, sigma=0.01)
+    B0, C0 = W.init_factors(M, N, K, 21)
+    f1 = run(did, X, B0, C0, 5, did.DID_ORDER_DID_BATCHED)[2][-1]
+    f4 = run(did, X, B0, C0, 5, did.DID_ORDER_DID_BATCHED, inner_c=4, inner_b=4)[2][-1]
+    r1 = O.factor(X, B0, C0, order="did", max_iter=5, stop="none")["trace"][-1]
+    r4 = O.factor(X, B0, C0, order="did", max_iter=5, stop="none", inner_c=4, inner_b=4)["trace"][-1]
+    print("5 sweeps: f(1,1) %.6g oracle %.6g ; f(4,4) %.6g oracle %.6g" % (f1, r1, f4, r4))
+    assert (f4 < f1) == (r4 < r1)
+
+
+def test_inner_repeats_rejected_outside_batched_order(did):
+    X, _, _ = W.planted(40, 60, 3, seed=1, sigma=0.01)
+    for order, kw in [(did.DID_ORDER_INTERLEAVED, dict(inner_c=2)), (did.DID_ORDER_DID, dict(inner_b=3)),
+                      (did.DID_ORDER_DID_BATCHED, dict(inner_c=65)), (did.DID_ORDER_DID_BATCHED, dict(inner_b=-1))]:
+        with pytest.raises(did.DIDError):
+            did.Context(np.ascontiguousarray(X.T), 40, 60, 3, order=order, **kw)
