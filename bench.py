@@ -239,6 +239,7 @@ def order_bench(did, X, M, N, K, w, seed, stream, order, steps, warmup, flags=0,
     trace = c.trace()
     c.close()
     out = {"order": order, "gemm": "bf16x9 emulation" if flags & did.DID_FLAG_GEMM_BF16X9 else "float32 SIMT",
+           "writeback": "eager" if flags & did.DID_FLAG_EAGER_WRITEBACK else "deferred",
            "inner": list(inner), "trace": [float(v) for v in trace],
            "value": steps / (ms / 1000.0), "unit": "sweeps/s", "ms_per_sweep": ms / steps,
            "objective_after": f, "sweeps": warmup + steps,
@@ -267,6 +268,12 @@ def batched_roofline(M, N, K, ms_per_sweep, bf16x9):
     return {"bound": "tensor", "achieved": 9 * tf, "peak": peak, "unit": "TFLOP/s (bf16 products)",
             "frac": 9 * tf / peak, "flops_per_sweep": fl, "peak_kind": kind,
             "note": "whole sweep; float32 flops x 9 bfloat16 products of the BF16x9 emulation"}
+
+
+def sweep_passes(K, lazy):
+    """Passes over R per sweep of the interleaved kernel: a read and a write per
+    k, less one write for each deferred k (pairs (k, k+1) share a write)."""
+    return 2 * K - (K // 2 if lazy else 0)
 
 
 def dist_env():
@@ -314,6 +321,8 @@ def main():
                          "(Algorithm 2), or the batched form of Algorithm 3")
     ap.add_argument("--gemm", default="pedantic", choices=["pedantic", "bf16x9"],
                     help="GEMMs of the batched order: float32 SIMT or cuBLAS BF16x9 emulation")
+    ap.add_argument("--eager", action="store_true",
+                    help="interleaved order: write R after every k (no deferred write-back)")
     ap.add_argument("--no-orders", action="store_true",
                     help="skip the C-first and batched Algorithm 3 measurements on the same workload")
     ap.add_argument("--phases", action="store_true",
@@ -376,6 +385,8 @@ def main():
     if args.order == "did_batched" and prec != did.DID_FP32:
         ap.error("the batched order runs in float32 only")
     flags = did.DID_FLAG_PHASE_TIMES if args.phases else 0
+    if args.eager:
+        flags |= did.DID_FLAG_EAGER_WRITEBACK
     if args.order == "did_batched" and args.gemm == "bf16x9":
         flags |= did.DID_FLAG_GEMM_BF16X9
     ctx = did.Context(X, M, N, K, seed=seed, precision=prec, order=ORDERS[args.order],
@@ -422,7 +433,8 @@ def main():
     launches = info1["sweep_launches"] - info0["sweep_launches"]
     prologues = info1["prologue_launches"] - info0["prologue_launches"]
     kms = info1["sweep_kernel_ms"] - info0["sweep_kernel_ms"]
-    alg_bytes = args.steps * 2.0 * K * M * N * s_bytes + prologues * 1.0 * M * N * s_bytes
+    passes = sweep_passes(K, info1["lazy_writeback"]) if args.order == "interleaved" else 2 * K
+    alg_bytes = args.steps * float(passes) * M * N * s_bytes + prologues * 1.0 * M * N * s_bytes
     achieved = alg_bytes / (kms / 1000.0) / 1e9
     peak, peak_kind = measured_peaks()
     traffic = profiled_traffic(args.workload, args.precision)
@@ -459,11 +471,12 @@ def main():
         i1 = c16.info()
         ms16 = e0.elapsed_time(e1)
         kms16 = i1["sweep_kernel_ms"] - i0["sweep_kernel_ms"]
-        ab16 = args.steps * 2.0 * K * M * N * 2 + (i1["prologue_launches"] - i0["prologue_launches"]) * M * N * 2.0
+        ab16 = (args.steps * float(sweep_passes(K, i1["lazy_writeback"])) * M * N * 2
+                + (i1["prologue_launches"] - i0["prologue_launches"]) * M * N * 2.0)
         f16 = c16.objective()
         c16.close()
         v16 = ws * args.steps / (ms16 / 1000.0)
-        bf16 = {"value": v16, "unit": "sweeps/s", "ratio_vs_fp32": v16 / value,
+        bf16 = {"value": v16, "unit": "sweeps/s", "ratio_vs_fp32": v16 / value, "lazy": int(i1["lazy_writeback"]),
                 "roofline_frac": ab16 / (kms16 / 1e3) / 1e9 / peak,
                 "tc_refreshes": int(i1["tc_refreshes"] - i0["tc_refreshes"]),
                 "objective_after": f16,
@@ -474,17 +487,18 @@ def main():
     if not args.no_orders and prec == did.DID_FP32 and args.order == "interleaved":
         x9 = did.DID_FLAG_GEMM_BF16X9
         orders = [order_bench(did, X, M, N, K, w, seed, stream, o, args.steps, args.warmup, f, r)
-                  for o, f, r in (("did", 0, (1, 1)), ("did_batched", 0, (1, 1)), ("did_batched", x9, (1, 1)),
+                  for o, f, r in (("interleaved", did.DID_FLAG_EAGER_WRITEBACK, (1, 1)), ("did", 0, (1, 1)),
+                                  ("did_batched", 0, (1, 1)), ("did_batched", x9, (1, 1)),
                                   ("did_batched", x9, (2, 2)), ("did_batched", x9, (4, 4)))]
         # inner repeats: sweeps (and time) to reach the objective that plain batched sweeps reach
-        target = orders[2]["trace"][-1]
+        target = orders[3]["trace"][-1]
         for o in orders:
             o["ratio_vs_main"] = o["value"] / value
             hit = [i for i, v in enumerate(o.pop("trace")) if v <= target]
             o["sweeps_to_plain_final"] = hit[0] if hit else None
             o["ms_to_plain_final"] = hit[0] * o["ms_per_sweep"] if hit else None
         # the batched form runs 4 of the library's kernels per sweep next to cuBLAS SGEMMs
-        gpu_launches += args.steps + 4 * 4 * args.steps
+        gpu_launches += 2 * args.steps + 4 * 4 * args.steps
 
     e2e = None
     if not args.no_e2e:
@@ -531,8 +545,15 @@ def main():
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                     "frac": achieved / peak, "traffic": traffic if args.order == "interleaved" else None,
                     "kernel": "sweep_kernel", "peak_kind": peak_kind,
-                    "alg_bytes_per_sweep": 2.0 * K * M * N * s_bytes,
+                    "alg_bytes_per_sweep": float(passes) * M * N * s_bytes,
+                    "lazy_writeback": int(info1["lazy_writeback"]), "ring_stages": int(info1["ring_stages"]),
                     "kernel_ms_per_sweep": kms / max(1, args.steps)}
+
+    if bf16 is not None and orders:
+        eager32 = [o for o in orders if o["order"] == "interleaved" and o["writeback"] == "eager"]
+        if eager32:
+            bf16["ratio_vs_fp32_eager"] = bf16["value"] / eager32[0]["value"]
+        bf16["writeback"] = "deferred" if bf16.pop("lazy", 0) else "eager"
 
     if rank == 0:
         line = {

@@ -111,6 +111,16 @@ typedef struct {
  * operand split into three bfloat16 terms, all nine products accumulated in
  * float32) instead of pedantic float32 SIMT arithmetic. */
 #define DID_FLAG_GEMM_BF16X9 4
+/* did_options.flags (DID_ORDER_INTERLEAVED): deferred write-back defers the
+ * write of R for k to the pass for k+1 (one write per pair of k, three passes
+ * over R per pair instead of four).  It needs two more M-vectors of shared
+ * memory beside a ring of at least three column stages per group.  By default
+ * a float32 residual uses it where it fits and a bfloat16 residual does not
+ * (its passes are bound by the per-column work, which the deferred form
+ * raises).  EAGER forces one write per k; LAZY requests deferral for either
+ * precision.  did_info.lazy_writeback says which ran. */
+#define DID_FLAG_EAGER_WRITEBACK 8
+#define DID_FLAG_LAZY_WRITEBACK 16
 
 typedef struct {
     int64_t M, N;
@@ -135,6 +145,8 @@ typedef struct {
     double dense_kernel_ms;
     int64_t tc_refreshes;    /* refreshes done on the tensor cores */
     double tc_refresh_ms;    /* their device time (operand split + GEMM) */
+    int32_t lazy_writeback;  /* 1: the sweep defers the write of R in pairs of k */
+    int32_t ring_stages;     /* shared-memory column stages per column group */
 } did_info;
 
 /* Fill *opt with the defaults: FP32, interleaved order, no refresh,

@@ -31,6 +31,8 @@ DID_STOP_RELCHANGE, DID_STOP_PAPER_EPS = 0, 1
 DID_FLAG_PHASE_TIMES = 1
 DID_FLAG_SIMT_REFRESH = 2
 DID_FLAG_GEMM_BF16X9 = 4
+DID_FLAG_EAGER_WRITEBACK = 8
+DID_FLAG_LAZY_WRITEBACK = 16
 
 
 class did_options(ctypes.Structure):
@@ -65,6 +67,7 @@ class did_info(ctypes.Structure):
         ("sweep_kernel_ms", ctypes.c_double), ("dense_launches", ctypes.c_int64),
         ("dense_kernel_ms", ctypes.c_double), ("tc_refreshes", ctypes.c_int64),
         ("tc_refresh_ms", ctypes.c_double),
+        ("lazy_writeback", ctypes.c_int32), ("ring_stages", ctypes.c_int32),
     ]
 
 

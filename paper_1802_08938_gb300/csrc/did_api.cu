@@ -37,6 +37,7 @@ struct did_ctx {
   double* Sp = nullptr;
   double* OBJp = nullptr;
   float* bold = nullptr;
+  float* Cold = nullptr;            // c_k before a deferred pass (lazy write-back), N floats
   Ctrl* ctrl = nullptr;
   double* trace_dev = nullptr;
   unsigned long long* degen = nullptr;
@@ -255,6 +256,8 @@ did_status launch_sweeps(did_ctx* c, int n, int stop_rule, double tol, int* done
   a.Sp = c->Sp;
   a.OBJp = c->OBJp;
   a.bold = c->bold;
+  a.lazy = c->plan.lazy;
+  a.Cold = c->Cold;
   a.ctrl = c->ctrl;
   a.trace = c->trace_dev;
   a.degen = c->degen;
@@ -432,7 +435,10 @@ static did_status create_impl(did_ctx* c, const float* X, uint64_t seed) {
   const int64_t M = c->M, N = c->N;
   const int K = c->K;
   char err[256] = {0};
-  did_status st = did::plan_sweep(c->ld, c->N, c->bf16, c->opt.grid_ctas, 0, &c->plan, err, sizeof(err));
+  const bool want_lazy = c->opt.order == DID_ORDER_INTERLEAVED && !(c->opt.flags & DID_FLAG_EAGER_WRITEBACK) &&
+                         (!c->bf16 || (c->opt.flags & DID_FLAG_LAZY_WRITEBACK));
+  did_status st =
+      did::plan_sweep(c->ld, c->N, c->bf16, c->opt.grid_ctas, 0, &c->plan, err, sizeof(err), want_lazy);
   if (st != DID_OK) return fail(c, st, "%s", err);
   c->dense_grid = did::dense_grid();
   DID_CUDA(c, cudaEventCreate(&c->ev0));
@@ -458,6 +464,7 @@ static did_status create_impl(did_ctx* c, const float* X, uint64_t seed) {
   ALLOC(Sp, (size_t)2 * G * sizeof(double));
   ALLOC(OBJp, U * sizeof(double));
   ALLOC(bold, (size_t)c->ld * sizeof(float));
+  if (c->plan.lazy) ALLOC(Cold, (size_t)N * sizeof(float));
   ALLOC(ctrl, sizeof(Ctrl));
   ALLOC(trace_dev, sizeof(double) * kMaxSweepsPerLaunch);
   ALLOC(degen, sizeof(unsigned long long));
@@ -536,7 +543,9 @@ did_status did_create_ex(const float* X, int64_t M, int64_t N, int32_t K, uint64
       (o.order != DID_ORDER_INTERLEAVED && o.order != DID_ORDER_DID && o.order != DID_ORDER_DID_BATCHED) ||
       (o.order == DID_ORDER_DID_BATCHED && (o.precision != DID_FP32 || !did::batched_supported(K))) ||
       (o.stop != DID_STOP_RELCHANGE && o.stop != DID_STOP_PAPER_EPS) || o.refresh_every < 0 ||
-      o.debug_barrier_extra < 0 || (o.flags & ~(DID_FLAG_PHASE_TIMES | DID_FLAG_SIMT_REFRESH | DID_FLAG_GEMM_BF16X9)) ||
+      o.debug_barrier_extra < 0 || (o.flags & ~(DID_FLAG_PHASE_TIMES | DID_FLAG_SIMT_REFRESH | DID_FLAG_GEMM_BF16X9 | DID_FLAG_EAGER_WRITEBACK |
+                   DID_FLAG_LAZY_WRITEBACK)) ||
+      ((o.flags & DID_FLAG_EAGER_WRITEBACK) && (o.flags & DID_FLAG_LAZY_WRITEBACK)) ||
       o.inner_c < 0 || o.inner_c > 64 || o.inner_b < 0 || o.inner_b > 64 ||
       (o.order != DID_ORDER_DID_BATCHED && (o.inner_c > 1 || o.inner_b > 1)))
     return DID_EINVAL;
@@ -695,6 +704,8 @@ did_status did_get_info(did_ctx* c, did_info* info) {
   info->dense_kernel_ms = c->dense_ms;
   info->tc_refreshes = c->tc_refreshes;
   info->tc_refresh_ms = c->tc_ms;
+  info->lazy_writeback = c->plan.lazy;
+  info->ring_stages = c->plan.D;
   return DID_OK;
 }
 

@@ -306,10 +306,13 @@ struct SweepArgs {
   int tstamp_cap;     // number of k-steps that fit in tstamp
   int cta_begin;      // multi-instance launch: first CTA of this instance
   int cta_count;      // multi-instance launch: CTAs of this instance
+  int lazy;           // 1: deferred write-back in pairs of k (interleaved order)
+  float* Cold;        // [N] c_k before a deferred pass (lazy only)
 };
 
 struct SweepPlan {
   int grid, GS, NG, NR, D;
+  int lazy;           // shared memory holds the pending b vectors of a deferred pass
   Units units;
   int nunits, dynamic, npart;
   size_t smem;
@@ -318,8 +321,10 @@ struct SweepPlan {
 
 // Choose the column-group shape and grid for (ld, precision); fills *plan.
 // max_units: upper bound on units the caller's partial buffers hold (0 = no bound).
+// want_lazy: reserve shared memory for deferred write-back when a ring of at
+// least 3 stages per group still fits (plan->lazy says whether it did).
 did_status plan_sweep(int ld, int64_t N, bool bf16, int grid_override, int64_t max_units, SweepPlan* plan,
-                      char* err, size_t errlen);
+                      char* err, size_t errlen, bool want_lazy = false);
 cudaError_t launch_sweep(const SweepPlan& plan, const SweepArgs& args, cudaStream_t s);
 
 // Multi-instance sweeps (serving): one cooperative launch runs several

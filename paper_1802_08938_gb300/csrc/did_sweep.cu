@@ -15,7 +15,13 @@
 // The paper's column partition of X over nodes becomes column groups over
 // SMs; its single cross-node sum becomes the fixed-order grid reduction of the
 // per-CTA partials, bracketed by bounded grid barriers.  Each k costs one read
-// and one write of R.
+// and one write of R -- or, with deferred write-back, the k of a pair (k, k+1)
+// share one write: the pass for k reads R, updates c_k and forms the partials
+// for k+1 from the updated column in registers but stores nothing; the pass
+// for k+1 applies the pending rank-one change b_k c_k - b_k' c_k' to the
+// column it reads (its dot product takes it as two scalars, b_{k+1}'.b_k and
+// b_{k+1}'.b_k') and writes R once for both.  Three passes over R per pair
+// instead of four.
 //
 // Layout: R is ld x N column-major (ld = M rounded up to 16, padding rows are
 // zero and stay zero); B is ld x K column-major; C is K x N row-major.  A
@@ -75,14 +81,16 @@ __device__ __forceinline__ double group_sum_f64(double v, int GS, int g, int lt,
 // TMA bulk copies; it is reused for the per-group partials at the end of a
 // pass (NG x ld floats, which fit because D x sizeof(elem) >= 4).
 struct SweepSmem {
-  size_t bo, bnw, ring, red, redd, dscr, bc, meta, mbar, total;
+  size_t bo, bnw, pbo, pbn, ring, red, redd, dscr, bc, meta, mbar, total;
 };
 __host__ __device__ __forceinline__ size_t align128(size_t x) { return (x + 127) & ~(size_t)127; }
-__host__ __device__ __forceinline__ SweepSmem sweep_smem(int ld, int NG, int D, int elem_bytes) {
+__host__ __device__ __forceinline__ SweepSmem sweep_smem(int ld, int NG, int D, int elem_bytes, bool lazy) {
   SweepSmem L;
   size_t o = 0;
   L.bo = o;   o += align128((size_t)ld * sizeof(float));
   L.bnw = o;  o += elem_bytes == 2 ? align128((size_t)ld * sizeof(float)) : 0;   // BF16: b_k' planes
+  L.pbo = o;  o += lazy ? align128((size_t)ld * sizeof(float)) : 0;             // pending b_k (old)
+  L.pbn = o;  o += lazy ? align128((size_t)ld * sizeof(float)) : 0;             // pending b_k
   L.ring = o; o += align128((size_t)NG * D * ld * elem_bytes);
   L.red = o;  o += 512 * sizeof(float);
   L.redd = o; o += 16 * 16 * sizeof(double);
@@ -97,6 +105,8 @@ __host__ __device__ __forceinline__ SweepSmem sweep_smem(int ld, int NG, int D, 
 struct SmemPtrs {
   float* bo;              // previous b_k (kUpdateC)
   float* bnw;             // b_k' (BF16 residual: kept here instead of registers)
+  float* pbo;             // pending b_{k-1} before its update (deferred write-back)
+  float* pbn;             // pending b_{k-1}' (deferred write-back)
   unsigned char* ring;    // column stages
   float* red;             // group reduction slots / b-reduce scratch
   double* redd;           // group float64 reduction slots
@@ -120,9 +130,15 @@ struct SmemPtrs {
 // the stages this group has consumed since the launch (stage and phase).
 // Vector slots r < NR-1 are always inside the column (NR = ceil(nvec / GS));
 // only the last slot needs a bounds test.
-template <int NR, bool BF16, int MODE, bool OBJ, bool GEN>
+// LZ (kUpdateC only): 0 plain; 1 deferred -- no store of R, c_k before the
+// update saved to a.Cold; 2 applying -- the column read is R without the
+// pending change b_{k-1} c_{k-1} - b_{k-1}' c_{k-1}' (pbo, pbn, a.Cold and C
+// row k-1), which the dot takes as beta_o c_old - beta_n c_new (beta_o =
+// b_k'.b_{k-1}, beta_n = b_k'.b_{k-1}') and the update adds before storing.
+template <int NR, bool BF16, int MODE, bool OBJ, bool GEN, int LZ = 0>
 __device__ __forceinline__ void column_pass(const SweepArgs& a, int cta, int k, int knext, float inv_bb,
-                                            float alpha, bool cdeg, const SmemPtrs& sm, unsigned& it, int pass) {
+                                            float alpha, bool cdeg, const SmemPtrs& sm, unsigned& it, int pass,
+                                            float beta_o = 0.f, float beta_n = 0.f) {
   typedef Vec<BF16> V;
   typedef typename V::raw raw;
   constexpr int VR = V::kRows;
@@ -233,6 +249,7 @@ __device__ __forceinline__ void column_pass(const SweepArgs& a, int cta, int k, 
   int64_t cu = -1, cu_lo = 0, cu_hi = 0;   // unit being consumed and its column range
   const float* Ck = Cw;
   const float* Cn = a.C + (int64_t)knext * N;
+  const float* Cp = a.C + (int64_t)(LZ == 2 ? k - 1 : k) * N;   // c_{k-1}' (applying pass)
   float co0 = 0.f, co1 = 0.f, cn0 = 0.f, cn1 = 0.f;
   int64_t pf_j = -1;                        // column the prefetched co0/cn0 belong to
 
@@ -288,6 +305,11 @@ __device__ __forceinline__ void column_pass(const SweepArgs& a, int cta, int k, 
       cn1 = __ldcg(Cn + j + 2);
     }
     pf_j = j + 1;
+    float cpo = 0.f, cpn = 0.f;             // pending c_{k-1,j} before and after its update
+    if (LZ == 2) {
+      cpo = __ldcg(a.Cold + j);
+      cpn = __ldcg(Cp + j);
+    }
     // Once every thread of the group has passed this column's reduction (or
     // barrier), all of them are done with the previous stage: refill it.
     auto refill_prev = [&]() {
@@ -316,14 +338,18 @@ __device__ __forceinline__ void column_pass(const SweepArgs& a, int cta, int k, 
           }
         }
       }
-      const float dot = group_sum(d2.x + d2.y, GS, g, lt, sm.red, parity);
+      float dot = group_sum(d2.x + d2.y, GS, g, lt, sm.red, parity);
       parity ^= 1;
       refill_prev();
+      if (LZ == 2) dot = fmaf(beta_o, cpo, fmaf(-beta_n, cpn, dot));
       if (!cdeg) {
         const float t = fmaf(alpha, c_old, dot * inv_bb);
         c_new = t > 0.f ? t : 0.f;
       }
-      if (lt == 0) __stcg(Cw + j, c_new);
+      if (lt == 0) {
+        __stcg(Cw + j, c_new);
+        if (LZ == 1) __stcg(a.Cold + j, c_old);
+      }
     } else {
       if (GS > 32) named_bar(1 + g, GS); else __syncwarp();
       refill_prev();
@@ -332,6 +358,8 @@ __device__ __forceinline__ void column_pass(const SweepArgs& a, int cta, int k, 
     const float2 co2 = make_float2(c_old, c_old);
     const float2 mcn2 = make_float2(-c_new, -c_new);
     const float2 cn2 = make_float2(cn, cn);
+    const float2 cpo2 = make_float2(cpo, cpo);
+    const float2 mcpn2 = make_float2(-cpn, -cpn);
 
     // Second read of the stage: update, store, accumulate.
     float2 s2 = make_float2(0.f, 0.f);
@@ -346,17 +374,27 @@ __device__ __forceinline__ void column_pass(const SweepArgs& a, int cta, int k, 
           for (int e = 0; e < VR; e += 4) {
             // BF16: the 8 previous-b values of vector q are stored as two
             // float4 half planes, so a warp's loads are contiguous 16-byte runs.
-            const float4 t =
-                *reinterpret_cast<const float4*>(bo_base + (BF16 ? (e / 4) * half + q * 4 : q * VR + e));
+            const int bi = BF16 ? (e / 4) * half + q * 4 : q * VR + e;
+            const float4 t = *reinterpret_cast<const float4*>(bo_base + bi);
+            float2 lo = make_float2(f[e], f[e + 1]);
+            float2 hi = make_float2(f[e + 2], f[e + 3]);
+            if (LZ == 2) {                  // the pending change of the deferred pass
+              const float4 tn = *reinterpret_cast<const float4*>(sm.pbn + bi);
+              const float4 to = *reinterpret_cast<const float4*>(sm.pbo + bi);
+              lo = __ffma2_rn(make_float2(tn.x, tn.y), mcpn2, lo);
+              hi = __ffma2_rn(make_float2(tn.z, tn.w), mcpn2, hi);
+              lo = __ffma2_rn(make_float2(to.x, to.y), cpo2, lo);
+              hi = __ffma2_rn(make_float2(to.z, to.w), cpo2, hi);
+            }
             float2 blo, bhi;
             bn_quad(r, e, blo, bhi);
-            float2 lo = __ffma2_rn(blo, mcn2, make_float2(f[e], f[e + 1]));
-            float2 hi = __ffma2_rn(bhi, mcn2, make_float2(f[e + 2], f[e + 3]));
+            lo = __ffma2_rn(blo, mcn2, lo);
+            hi = __ffma2_rn(bhi, mcn2, hi);
             lo = __ffma2_rn(make_float2(t.x, t.y), co2, lo);
             hi = __ffma2_rn(make_float2(t.z, t.w), co2, hi);
             f[e] = lo.x; f[e + 1] = lo.y; f[e + 2] = hi.x; f[e + 3] = hi.y;
           }
-          __stcs(Rcol + r * GS, V::pack(f));
+          if (LZ != 1) __stcs(Rcol + r * GS, V::pack(f));
         }
 #pragma unroll
         for (int h = 0; h < VH; ++h) {
@@ -480,10 +518,13 @@ __device__ __forceinline__ void b_reduce(const SweepArgs& a, int cta, int G, int
 template <int NR, bool BF16, bool GEN>
 __device__ __forceinline__ void sweep_body(const SweepArgs& a, int cta, int ncta) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  const SweepSmem L = sweep_smem(a.ld, a.NG, a.D, BF16 ? 2 : 4);
+  const bool lazy = !GEN && a.lazy;
+  const SweepSmem L = sweep_smem(a.ld, a.NG, a.D, BF16 ? 2 : 4, lazy);
   SmemPtrs sm;
   sm.bo = reinterpret_cast<float*>(smem_raw + L.bo);
   sm.bnw = reinterpret_cast<float*>(smem_raw + L.bnw);
+  sm.pbo = reinterpret_cast<float*>(smem_raw + L.pbo);
+  sm.pbn = reinterpret_cast<float*>(smem_raw + L.pbn);
   sm.ring = smem_raw + L.ring;
   sm.red = reinterpret_cast<float*>(smem_raw + L.red);
   sm.redd = reinterpret_cast<double*>(smem_raw + L.redd);
@@ -531,6 +572,28 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a, int cta, int ncta
       }
     }
     return block_sum_f64(nn, sm.dscr);   // includes the barrier before the pass
+  };
+  // Deferred write-back, before the applying pass for k: the pending pair
+  // (b_{k-1} from bo, b_{k-1}' from B) moves to pbo / pbn in bo's layout, and
+  // bc[0], bc[3] get b_k'.b_{k-1} and b_k'.b_{k-1}' (float64, same order in
+  // every CTA).  Each thread moves the same elements stage_b later rewrites.
+  auto stage_pending = [&](int k) {
+    const float* bprev = a.B + (size_t)(k - 1) * a.ld;
+    const float* bk = a.B + (size_t)k * a.ld;
+    double so = 0.0, sn = 0.0;
+    for (int i = threadIdx.x; i < a.ld; i += blockDim.x) {
+      const int dst = BF16 ? ((i & 7) >> 2) * (a.ld / 2) + (i >> 3) * 4 + (i & 3) : i;
+      const float vo = sm.bo[dst];
+      const float vn = __ldcg(bprev + i);
+      const float vk = __ldcg(bk + i);
+      sm.pbo[dst] = vo;
+      sm.pbn[dst] = vn;
+      so += (double)vk * (double)vo;
+      sn += (double)vk * (double)vn;
+    }
+    so = block_sum_f64(so, sm.dscr);
+    sn = block_sum_f64(sn, sm.dscr);
+    if (threadIdx.x == 0) { bc[0] = so; bc[3] = sn; }
   };
 
   const double f0 = a.f0;
@@ -607,6 +670,9 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a, int cta, int ncta
         const double bob = warp_sum_global_f64(a.Sp + 1, G, 2);
         if (l == 0) { bc[1] = bb; bc[2] = bob; }
       }
+      // Deferred write-back: k even with a partner k+1 defers, k odd applies.
+      const int lz = !lazy ? 0 : (k & 1) ? 2 : (k + 1 < a.K ? 1 : 0);
+      if (lz == 2) stage_pending(k);   // before stage_b rewrites bo
       stage_b(a.bold, a.B + (size_t)k * a.ld);
       const double bb = bc[1], bob = bc[2];
       const bool cdeg = !(bb > 0.0);
@@ -614,10 +680,21 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a, int cta, int ncta
       const float alpha = cdeg ? 0.f : (float)(bob / bb);
       if (cdeg && cta == 0 && threadIdx.x == 0) atomicAdd(a.degen, 1ull);
       const int knext = (k + 1 < a.K) ? k + 1 : 0;
-      if (k == a.K - 1)
+      if (lz == 2) {
+        const float beta_o = (float)bc[0], beta_n = (float)bc[3];
+        if (k == a.K - 1)
+          column_pass<NR, BF16, kUpdateC, true, GEN, 2>(a, cta, k, knext, inv_bb, alpha, cdeg, sm, it, pass++,
+                                                        beta_o, beta_n);
+        else
+          column_pass<NR, BF16, kUpdateC, false, GEN, 2>(a, cta, k, knext, inv_bb, alpha, cdeg, sm, it, pass++,
+                                                         beta_o, beta_n);
+      } else if (lz == 1) {
+        column_pass<NR, BF16, kUpdateC, false, GEN, 1>(a, cta, k, knext, inv_bb, alpha, cdeg, sm, it, pass++);
+      } else if (k == a.K - 1) {
         column_pass<NR, BF16, kUpdateC, true, GEN>(a, cta, k, knext, inv_bb, alpha, cdeg, sm, it, pass++);
-      else
+      } else {
         column_pass<NR, BF16, kUpdateC, false, GEN>(a, cta, k, knext, inv_bb, alpha, cdeg, sm, it, pass++);
+      }
       if (rec) a.tstamp[4 * step + 2] = globaltimer_ns();
       DID_GRID_SYNC();
       if (rec) a.tstamp[4 * step + 3] = globaltimer_ns();
@@ -698,7 +775,7 @@ const void* pick_func(bool bf16, int NR) {
 }  // namespace
 
 did_status plan_sweep(int ld, int64_t N, bool bf16, int grid_override, int64_t max_units, SweepPlan* plan,
-                      char* err, size_t errlen) {
+                      char* err, size_t errlen, bool want_lazy) {
   const int VR = bf16 ? 8 : 4;
   const int elem = bf16 ? 2 : 4;
   const int nvec = ld / VR;
@@ -720,7 +797,7 @@ did_status plan_sweep(int ld, int64_t N, bool bf16, int grid_override, int64_t m
     if (NR > nr_max) continue;
     const int NG = kSweepThreads / GS;
     const int waste = GS * NR - nvec;
-    const bool fits3 = sweep_smem(ld, NG, 3, elem).total <= budget;
+    const bool fits3 = sweep_smem(ld, NG, 3, elem, false).total <= budget;
     const bool good = fits3 && waste * 8 <= GS * NR;
     const long key = good ? (1L << 40) + ((long)NG << 20) - waste : (long)(1 << 20) - waste;
     if (key > best_key) { best_key = key; best_gs = GS; best_nr = NR; }
@@ -747,16 +824,25 @@ did_status plan_sweep(int ld, int64_t N, bool bf16, int grid_override, int64_t m
     snprintf(err, errlen, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
     return DID_ECUDA;
   }
-  // Deepest ring (2..6 stages per group) that fits the shared memory.
+  // Deepest ring (2..6 stages per group) that fits the shared memory; with
+  // deferred write-back (two more ld-vectors) only if 3 stages still fit.
   plan->D = 0;
-  for (int D = 6; D >= 2; --D) {
-    if (sweep_smem(ld, plan->NG, D, elem).total <= budget) { plan->D = D; break; }
+  plan->lazy = 0;
+  if (want_lazy) {
+    for (int D = 6; D >= 3; --D) {
+      if (sweep_smem(ld, plan->NG, D, elem, true).total <= budget) { plan->D = D; plan->lazy = 1; break; }
+    }
+  }
+  if (!plan->lazy) {
+    for (int D = 6; D >= 2; --D) {
+      if (sweep_smem(ld, plan->NG, D, elem, false).total <= budget) { plan->D = D; break; }
+    }
   }
   if (plan->D == 0) {
     snprintf(err, errlen, "sweep shared memory for ld=%d exceeds the per-CTA limit", ld);
     return DID_E_TOO_LARGE;
   }
-  plan->smem = sweep_smem(ld, plan->NG, plan->D, elem).total;
+  plan->smem = sweep_smem(ld, plan->NG, plan->D, elem, plan->lazy != 0).total;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan->func, kSweepThreads, plan->smem);
   if (e != cudaSuccess || per_sm < 1) {
@@ -844,9 +930,10 @@ did_status plan_instance(int ld, int64_t N, bool bf16, int ncta, size_t smem_bud
   plan->NG = kSweepThreads / GS;
   plan->D = 0;
   for (int D = 6; D >= 2; --D)
-    if (sweep_smem(ld, plan->NG, D, elem).total <= smem_budget) { plan->D = D; break; }
+    if (sweep_smem(ld, plan->NG, D, elem, false).total <= smem_budget) { plan->D = D; break; }
   if (plan->D == 0) return DID_E_TOO_LARGE;
-  plan->smem = sweep_smem(ld, plan->NG, plan->D, elem).total;
+  plan->lazy = 0;
+  plan->smem = sweep_smem(ld, plan->NG, plan->D, elem, false).total;
   plan->grid = ncta;
   plan->func = serve_func(bf16);
   const int64_t TG = (int64_t)ncta * plan->NG;
