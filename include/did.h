@@ -121,6 +121,12 @@ typedef struct {
  * precision.  did_info.lazy_writeback says which ran. */
 #define DID_FLAG_EAGER_WRITEBACK 8
 #define DID_FLAG_LAZY_WRITEBACK 16
+/* did_options.flags (DID_ORDER_INTERLEAVED): c-passes take one column per
+ * step of a column group.  By default a group takes two consecutive columns
+ * of its unit per step where the ring has four or more stages, in the passes
+ * bound by per-column work (a bfloat16 residual; the deferred pass of a
+ * float32 one); the results are bitwise the same (for comparisons). */
+#define DID_FLAG_SINGLE_COLUMNS 32
 
 typedef struct {
     int64_t M, N;
@@ -147,6 +153,7 @@ typedef struct {
     double tc_refresh_ms;    /* their device time (operand split + GEMM) */
     int32_t lazy_writeback;  /* 1: the sweep defers the write of R in pairs of k */
     int32_t ring_stages;     /* shared-memory column stages per column group */
+    int32_t column_pairs;    /* 1: a column group takes two columns per step of a c-pass */
 } did_info;
 
 /* Fill *opt with the defaults: FP32, interleaved order, no refresh,

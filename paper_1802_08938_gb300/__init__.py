@@ -33,6 +33,7 @@ DID_FLAG_SIMT_REFRESH = 2
 DID_FLAG_GEMM_BF16X9 = 4
 DID_FLAG_EAGER_WRITEBACK = 8
 DID_FLAG_LAZY_WRITEBACK = 16
+DID_FLAG_SINGLE_COLUMNS = 32
 
 
 class did_options(ctypes.Structure):
@@ -68,6 +69,7 @@ class did_info(ctypes.Structure):
         ("dense_kernel_ms", ctypes.c_double), ("tc_refreshes", ctypes.c_int64),
         ("tc_refresh_ms", ctypes.c_double),
         ("lazy_writeback", ctypes.c_int32), ("ring_stages", ctypes.c_int32),
+        ("column_pairs", ctypes.c_int32),
     ]
 
 

@@ -258,6 +258,7 @@ did_status launch_sweeps(did_ctx* c, int n, int stop_rule, double tol, int* done
   a.bold = c->bold;
   a.lazy = c->plan.lazy;
   a.Cold = c->Cold;
+  a.pair = c->opt.order == DID_ORDER_INTERLEAVED && !(c->opt.flags & DID_FLAG_SINGLE_COLUMNS) ? c->plan.pair : 0;
   a.ctrl = c->ctrl;
   a.trace = c->trace_dev;
   a.degen = c->degen;
@@ -544,7 +545,7 @@ did_status did_create_ex(const float* X, int64_t M, int64_t N, int32_t K, uint64
       (o.order == DID_ORDER_DID_BATCHED && (o.precision != DID_FP32 || !did::batched_supported(K))) ||
       (o.stop != DID_STOP_RELCHANGE && o.stop != DID_STOP_PAPER_EPS) || o.refresh_every < 0 ||
       o.debug_barrier_extra < 0 || (o.flags & ~(DID_FLAG_PHASE_TIMES | DID_FLAG_SIMT_REFRESH | DID_FLAG_GEMM_BF16X9 | DID_FLAG_EAGER_WRITEBACK |
-                   DID_FLAG_LAZY_WRITEBACK)) ||
+                   DID_FLAG_LAZY_WRITEBACK | DID_FLAG_SINGLE_COLUMNS)) ||
       ((o.flags & DID_FLAG_EAGER_WRITEBACK) && (o.flags & DID_FLAG_LAZY_WRITEBACK)) ||
       o.inner_c < 0 || o.inner_c > 64 || o.inner_b < 0 || o.inner_b > 64 ||
       (o.order != DID_ORDER_DID_BATCHED && (o.inner_c > 1 || o.inner_b > 1)))
@@ -706,6 +707,8 @@ did_status did_get_info(did_ctx* c, did_info* info) {
   info->tc_refresh_ms = c->tc_ms;
   info->lazy_writeback = c->plan.lazy;
   info->ring_stages = c->plan.D;
+  info->column_pairs =
+      c->opt.order == DID_ORDER_INTERLEAVED && !(c->opt.flags & DID_FLAG_SINGLE_COLUMNS) ? c->plan.pair : 0;
   return DID_OK;
 }
 

@@ -308,11 +308,13 @@ struct SweepArgs {
   int cta_count;      // multi-instance launch: CTAs of this instance
   int lazy;           // 1: deferred write-back in pairs of k (interleaved order)
   float* Cold;        // [N] c_k before a deferred pass (lazy only)
+  int pair;           // 1: column groups take two columns per iteration (needs D >= 4)
 };
 
 struct SweepPlan {
   int grid, GS, NG, NR, D;
   int lazy;           // shared memory holds the pending b vectors of a deferred pass
+  int pair;           // c-passes take columns in pairs
   Units units;
   int nunits, dynamic, npart;
   size_t smem;

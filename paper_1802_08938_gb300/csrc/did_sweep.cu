@@ -89,6 +89,8 @@ did_status plan_sweep(int ld, int64_t N, bool bf16, int grid_override, int64_t m
     return DID_E_TOO_LARGE;
   }
   plan->smem = sweep_smem(ld, plan->NG, plan->D, elem, plan->lazy != 0).total;
+  // Column pairs need a second stage issued before the first one's barrier.
+  plan->pair = kPairs && plan->D >= 4 ? 1 : 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan->func, kSweepThreads, plan->smem);
   if (e != cudaSuccess || per_sm < 1) {
@@ -173,6 +175,7 @@ did_status plan_instance(int ld, int64_t N, bool bf16, int ncta, size_t smem_bud
     if (sweep_smem(ld, plan->NG, D, elem, false).total <= smem_budget) { plan->D = D; break; }
   if (plan->D == 0) return DID_E_TOO_LARGE;
   plan->lazy = 0;
+  plan->pair = 0;
   plan->smem = sweep_smem(ld, plan->NG, plan->D, elem, false).total;
   plan->grid = ncta;
   plan->func = serve_func(bf16);

@@ -48,6 +48,10 @@ constexpr int kMaxNrBf16 = 5;
 #define DID_MAX_STAGES 6
 #endif
 constexpr int kMaxStages = DID_MAX_STAGES;   // ring stages per column group (upper bound)
+#ifndef DID_PAIRS
+#define DID_PAIRS 1
+#endif
+constexpr bool kPairs = DID_PAIRS != 0;      // c-passes may take columns in pairs
 
 // Sum v over the GS threads of a column group; every thread of the group gets
 // the same value (xor tree within warps, then the warps' totals in order).
@@ -61,6 +65,28 @@ __device__ __forceinline__ float group_sum(float v, int GS, int g, int lt, float
   float s = 0.f;
   for (int i = 0; i < nw; ++i) s += slot[i];
   return s;
+}
+
+// Two sums over the GS threads of a column group at once (the two columns of
+// a pair; same order as two group_sum calls).  Slots: 2 floats per warp,
+// 32 per group, so GS > 32 implies at most 8 groups.
+__device__ __forceinline__ float2 group_sum2(float2 v, int GS, int g, int lt, float* red, int parity) {
+  v.x = warp_sum_f32(v.x);
+  v.y = warp_sum_f32(v.y);
+  if (GS <= 32) return v;
+  float* slot = red + parity * (16 * 16) + g * 32;
+  const int nw = GS >> 5;
+  if ((lt & 31) == 0) {
+    slot[2 * (lt >> 5)] = v.x;
+    slot[2 * (lt >> 5) + 1] = v.y;
+  }
+  named_bar(1 + g, GS);
+  float2 t = make_float2(0.f, 0.f);
+  for (int i = 0; i < nw; ++i) {
+    t.x += slot[2 * i];
+    t.y += slot[2 * i + 1];
+  }
+  return t;
 }
 
 // float64 sum over the GS threads of a column group (same scheme as group_sum).
@@ -135,7 +161,13 @@ struct SmemPtrs {
 // pending change b_{k-1} c_{k-1} - b_{k-1}' c_{k-1}' (pbo, pbn, a.Cold and C
 // row k-1), which the dot takes as beta_o c_old - beta_n c_new (beta_o =
 // b_k'.b_{k-1}, beta_n = b_k'.b_{k-1}') and the update adds before storing.
-template <int NR, bool BF16, int MODE, bool OBJ, bool GEN, int LZ = 0>
+// NC = 2 (pairs): a group takes two consecutive columns of its unit per
+// iteration -- one load of the b vectors and one group reduction serve both,
+// and the two dot products are independent chains.  Needs D >= 4 (the second
+// stage of an iteration was issued before the first's barrier); a unit with
+// an odd count ends with a single column.  Results equal the NC = 1 pass bit
+// for bit (every sum takes the columns in the same order).
+template <int NR, bool BF16, int MODE, bool OBJ, bool GEN, int LZ = 0, int NC = 1>
 __device__ __forceinline__ void column_pass(const SweepArgs& a, int cta, int k, int knext, float inv_bb,
                                             float alpha, bool cdeg, const SmemPtrs& sm, unsigned& it, int pass,
                                             float beta_o = 0.f, float beta_n = 0.f) {
@@ -277,6 +309,198 @@ __device__ __forceinline__ void column_pass(const SweepArgs& a, int cta, int k, 
     }
   };
 
+  if constexpr (NC == 2) {
+    unsigned prev_st[2] = {0u, 0u};
+    int prev_n = 0;
+    int64_t pf_j = -1;                      // first column of the prefetched pair
+    float pco[2] = {0.f, 0.f}, pcn[2] = {0.f, 0.f};
+    bool done = false;
+    while (!done) {
+      int64_t jj[2] = {0, 0};
+      unsigned sts[2] = {0u, 0u};
+      int nc = 0;
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const unsigned st = it % D;
+        mbar_wait_bounded(bars + st, (it / D) & 1u, err, timeout_ns);
+        const int64_t j = meta[st];
+        if (j < 0) {                        // end of the stream: consumed
+          ++it;
+          done = true;
+          break;
+        }
+        if (j < cu_lo || j >= cu_hi) {
+          if (c == 1) break;                // next unit: left for the next iteration
+          flush(cu);                        // first column of a new unit
+          cu = unit_of(UN, j);
+          unit_range(UN, N, cu, cu_lo, cu_hi);
+        }
+        jj[c] = j;
+        sts[c] = st;
+        ++it;
+        ++nc;
+      }
+      if (nc == 0) break;
+      const bool two = nc == 2;
+      float co[2], cx[2], cpo[2] = {0.f, 0.f}, cpn[2] = {0.f, 0.f};
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const int64_t jc = two ? jj[c] : jj[0];
+        if (jj[0] == pf_j) {
+          co[c] = pco[c];
+          cx[c] = pcn[c];
+        } else {
+          co[c] = MODE != kPrologue ? __ldcg(Ck + jc) : 0.f;
+          cx[c] = __ldcg(Cn + jc);
+        }
+        if (LZ == 2) {
+          cpo[c] = __ldcg(a.Cold + jc);
+          cpn[c] = __ldcg(Cp + jc);
+        }
+      }
+      {                                     // the next pair of this unit
+        const int64_t nj = jj[nc - 1] + 1;
+        pf_j = nj < cu_hi ? nj : -1;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          if (nj + c < cu_hi) {
+            if (MODE != kPrologue) pco[c] = __ldcg(Ck + nj + c);
+            pcn[c] = __ldcg(Cn + nj + c);
+          }
+        }
+      }
+      auto refill_prev = [&]() {
+        if (lt == 0) {
+          fence_proxy_async_shared();
+          for (int q = 0; q < prev_n; ++q) issue(prev_st[q]);
+        }
+      };
+      const raw* stage0 = reinterpret_cast<const raw*>(ring + (size_t)sts[0] * colbytes) + lt;
+      const raw* stage1 = reinterpret_cast<const raw*>(ring + (size_t)(two ? sts[1] : sts[0]) * colbytes) + lt;
+      raw* Rcol0 = reinterpret_cast<raw*>(a.R) + jj[0] * nvec + lt;
+      raw* Rcol1 = reinterpret_cast<raw*>(a.R) + (two ? jj[1] : jj[0]) * nvec + lt;
+
+      float cnew[2] = {co[0], co[1]};
+      if (MODE == kUpdateC) {
+        float2 da = make_float2(0.f, 0.f), db = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          if (slot_ok(r)) {
+            float f0[VR], f1[VR];
+            V::unpack(stage0[r * GS], f0);
+            V::unpack(stage1[r * GS], f1);
+#pragma unroll
+            for (int e = 0; e < VR; e += 4) {
+              float2 blo, bhi;
+              bn_quad(r, e, blo, bhi);
+              da = __ffma2_rn(blo, make_float2(f0[e], f0[e + 1]), da);
+              da = __ffma2_rn(bhi, make_float2(f0[e + 2], f0[e + 3]), da);
+              db = __ffma2_rn(blo, make_float2(f1[e], f1[e + 1]), db);
+              db = __ffma2_rn(bhi, make_float2(f1[e + 2], f1[e + 3]), db);
+            }
+          }
+        }
+        const float2 dot2 = group_sum2(make_float2(da.x + da.y, db.x + db.y), GS, g, lt, sm.red, parity);
+        parity ^= 1;
+        refill_prev();
+        float dots[2] = {dot2.x, dot2.y};
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          if (LZ == 2) dots[c] = fmaf(beta_o, cpo[c], fmaf(-beta_n, cpn[c], dots[c]));
+          if (!cdeg) {
+            const float t = fmaf(alpha, co[c], dots[c] * inv_bb);
+            cnew[c] = t > 0.f ? t : 0.f;
+          }
+        }
+        if (lt == 0) {
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            if (c == 0 || two) {
+              __stcg(Cw + jj[c], cnew[c]);
+              if (LZ == 1) __stcg(a.Cold + jj[c], co[c]);
+            }
+          }
+        }
+      } else {
+        if (GS > 32) named_bar(1 + g, GS); else __syncwarp();
+        refill_prev();
+      }
+      prev_n = nc;
+      prev_st[0] = sts[0];
+      prev_st[1] = sts[1];
+
+      float cn[2];
+#pragma unroll
+      for (int c = 0; c < 2; ++c) cn[c] = (knext == k && MODE == kUpdateC) ? cnew[c] : cx[c];
+      float2 sa = make_float2(0.f, 0.f), sb = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        if (slot_ok(r)) {
+          const int q = lt + r * GS;
+          float f0[VR], f1[VR];
+          V::unpack(stage0[r * GS], f0);
+          V::unpack(stage1[r * GS], f1);
+          if (MODE != kPrologue) {
+#pragma unroll
+            for (int e = 0; e < VR; e += 4) {
+              const int bi = BF16 ? (e / 4) * half + q * 4 : q * VR + e;
+              const float4 t = *reinterpret_cast<const float4*>(bo_base + bi);
+              float2 blo, bhi;
+              bn_quad(r, e, blo, bhi);
+              float4 tn = make_float4(0.f, 0.f, 0.f, 0.f), to = tn;
+              if (LZ == 2) {
+                tn = *reinterpret_cast<const float4*>(sm.pbn + bi);
+                to = *reinterpret_cast<const float4*>(sm.pbo + bi);
+              }
+#pragma unroll
+              for (int c = 0; c < 2; ++c) {
+                float* f = c == 0 ? f0 : f1;
+                float2 lo = make_float2(f[e], f[e + 1]);
+                float2 hi = make_float2(f[e + 2], f[e + 3]);
+                if (LZ == 2) {
+                  const float2 mp = make_float2(-cpn[c], -cpn[c]), po = make_float2(cpo[c], cpo[c]);
+                  lo = __ffma2_rn(make_float2(tn.x, tn.y), mp, lo);
+                  hi = __ffma2_rn(make_float2(tn.z, tn.w), mp, hi);
+                  lo = __ffma2_rn(make_float2(to.x, to.y), po, lo);
+                  hi = __ffma2_rn(make_float2(to.z, to.w), po, hi);
+                }
+                const float2 mc = make_float2(-cnew[c], -cnew[c]), oc = make_float2(co[c], co[c]);
+                lo = __ffma2_rn(blo, mc, lo);
+                hi = __ffma2_rn(bhi, mc, hi);
+                lo = __ffma2_rn(make_float2(t.x, t.y), oc, lo);
+                hi = __ffma2_rn(make_float2(t.z, t.w), oc, hi);
+                f[e] = lo.x; f[e + 1] = lo.y; f[e + 2] = hi.x; f[e + 3] = hi.y;
+              }
+            }
+            if (LZ != 1) {
+              __stcs(Rcol0 + r * GS, V::pack(f0));
+              if (two) __stcs(Rcol1 + r * GS, V::pack(f1));
+            }
+          }
+          const float2 n0 = make_float2(cn[0], cn[0]), n1 = make_float2(cn[1], cn[1]);
+#pragma unroll
+          for (int h = 0; h < VH; ++h) {
+            const float2 fa = make_float2(f0[2 * h], f0[2 * h + 1]);
+            p[r][h] = __ffma2_rn(fa, n0, p[r][h]);
+            if (OBJ) sa = __ffma2_rn(fa, fa, sa);
+            if (two) {
+              const float2 fb = make_float2(f1[2 * h], f1[2 * h + 1]);
+              p[r][h] = __ffma2_rn(fb, n1, p[r][h]);
+              if (OBJ) sb = __ffma2_rn(fb, fb, sb);
+            }
+          }
+        }
+      }
+      if (lt == 0) {
+        cc_acc += (double)cn[0] * (double)cn[0];
+        if (two) cc_acc += (double)cn[1] * (double)cn[1];
+      }
+      if (OBJ) {
+        obj_acc += (double)(sa.x + sa.y);
+        if (two) obj_acc += (double)(sb.x + sb.y);
+      }
+    }
+  } else {
   for (int64_t i = 0;; ++i) {
     const unsigned st = it % D;
     mbar_wait_bounded(bars + st, (it / D) & 1u, err, timeout_ns);
@@ -407,6 +631,7 @@ __device__ __forceinline__ void column_pass(const SweepArgs& a, int cta, int k, 
     if (lt == 0) cc_acc += (double)cn * (double)cn;
     if (OBJ) obj_acc += (double)(s2.x + s2.y);
   }
+  }   // NC == 1
   flush(cu);
   // R written here is read by TMA (async proxy) in the next pass.
   if (MODE != kPrologue) fence_proxy_async_global();
@@ -680,9 +905,27 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a, int cta, int ncta
       const float alpha = cdeg ? 0.f : (float)(bob / bb);
       if (cdeg && cta == 0 && threadIdx.x == 0) atomicAdd(a.degen, 1ull);
       const int knext = (k + 1 < a.K) ? k + 1 : 0;
-      if (lz == 2) {
-        const float beta_o = (float)bc[0], beta_n = (float)bc[3];
-        if (k == a.K - 1)
+      const float beta_o = lz == 2 ? (float)bc[0] : 0.f, beta_n = lz == 2 ? (float)bc[3] : 0.f;
+      const bool last = k == a.K - 1;
+      // Pairs pay off where a pass is bound by per-column work: a bfloat16
+      // residual, and the deferred (read-only) pass of a float32 one.
+      if (!GEN && a.pair && (BF16 || lz == 1)) {
+        if (lz == 2) {
+          if (last)
+            column_pass<NR, BF16, kUpdateC, true, GEN, 2, 2>(a, cta, k, knext, inv_bb, alpha, cdeg, sm, it, pass++,
+                                                             beta_o, beta_n);
+          else
+            column_pass<NR, BF16, kUpdateC, false, GEN, 2, 2>(a, cta, k, knext, inv_bb, alpha, cdeg, sm, it,
+                                                              pass++, beta_o, beta_n);
+        } else if (lz == 1) {
+          column_pass<NR, BF16, kUpdateC, false, GEN, 1, 2>(a, cta, k, knext, inv_bb, alpha, cdeg, sm, it, pass++);
+        } else if (last) {
+          column_pass<NR, BF16, kUpdateC, true, GEN, 0, 2>(a, cta, k, knext, inv_bb, alpha, cdeg, sm, it, pass++);
+        } else {
+          column_pass<NR, BF16, kUpdateC, false, GEN, 0, 2>(a, cta, k, knext, inv_bb, alpha, cdeg, sm, it, pass++);
+        }
+      } else if (lz == 2) {
+        if (last)
           column_pass<NR, BF16, kUpdateC, true, GEN, 2>(a, cta, k, knext, inv_bb, alpha, cdeg, sm, it, pass++,
                                                         beta_o, beta_n);
         else
@@ -690,7 +933,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a, int cta, int ncta
                                                          beta_o, beta_n);
       } else if (lz == 1) {
         column_pass<NR, BF16, kUpdateC, false, GEN, 1>(a, cta, k, knext, inv_bb, alpha, cdeg, sm, it, pass++);
-      } else if (k == a.K - 1) {
+      } else if (last) {
         column_pass<NR, BF16, kUpdateC, true, GEN>(a, cta, k, knext, inv_bb, alpha, cdeg, sm, it, pass++);
       } else {
         column_pass<NR, BF16, kUpdateC, false, GEN>(a, cta, k, knext, inv_bb, alpha, cdeg, sm, it, pass++);

@@ -103,3 +103,36 @@ def test_lazy_stopping_and_resume(did):
         assert ctx.info()["lazy_writeback"] == 1
     print("lazy stopping: GPU %d sweeps, oracle %d" % (iters, ref["iters"]))
     assert iters == ref["iters"]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_lazy_bitwise_deterministic(did, prec):
+    M, N, K = 2000, 30000, 6
+    X, _, _ = W.planted(M, N, K, seed=11, sigma=0.02)
+    B0, C0 = W.init_factors(M, N, K, 11)
+    kw = dict(flags=did.DID_FLAG_LAZY_WRITEBACK)
+    if prec == "bf16":
+        kw["precision"] = did.DID_BF16R
+    a = run(did, X, B0, C0, 6, **kw)
+    b = run(did, X, B0, C0, 6, **kw)
+    assert a["info"]["lazy_writeback"] == 1
+    assert np.array_equal(a["B"], b["B"]) and np.array_equal(a["C"], b["C"])
+    assert np.array_equal(a["trace"], b["trace"])
+
+
+@pytest.mark.parametrize("lazy", [False, True])
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_column_pairs_equal_single_columns(did, prec, lazy):
+    """Pairs take the same sums in the same order: bitwise equal results."""
+    M, N, K = 1500, 20001, 5                   # odd N: units end with a single column
+    X, _, _ = W.planted(M, N, K, seed=12, sigma=0.02)
+    B0, C0 = W.init_factors(M, N, K, 12)
+    kw = dict(precision=did.DID_BF16R) if prec == "bf16" else {}
+    kw["flags"] = did.DID_FLAG_LAZY_WRITEBACK if lazy else did.DID_FLAG_EAGER_WRITEBACK
+    a = run(did, X, B0, C0, 4, **kw)
+    kw["flags"] |= did.DID_FLAG_SINGLE_COLUMNS
+    b = run(did, X, B0, C0, 4, **kw)
+    print("pairs %s lazy=%s: pair=%d stages=%d" % (prec, lazy, a["info"]["column_pairs"], a["info"]["ring_stages"]))
+    assert b["info"]["column_pairs"] == 0
+    assert np.array_equal(a["B"], b["B"]) and np.array_equal(a["C"], b["C"])
+    assert np.array_equal(a["trace"], b["trace"])
