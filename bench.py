@@ -51,7 +51,8 @@ CPU_SAMPLE_COLS = {"planted_exp_5000x200000_k50": 1000, "image_like_784x70000_k1
                    "salt_10000x500000_k100": 250, "planted_uniform_200x1000_k10": 1000}
 CPU_SAMPLE_SWEEPS = 3
 
-SWEEP_SOURCES = ["paper_1802_08938_gb300/csrc/did_sweep.cu", "paper_1802_08938_gb300/csrc/did_internal.cuh"]
+SWEEP_SOURCES = ["paper_1802_08938_gb300/csrc/did_sweep.cu", "paper_1802_08938_gb300/csrc/did_sweep_kernel.cuh",
+                 "paper_1802_08938_gb300/csrc/did_internal.cuh"]
 
 
 def sweep_source_hash():
