@@ -77,3 +77,65 @@ def test_host_side_argument_checks_need_no_gpu(lib):
     assert did._lib.did_create(x, 4, 4, 5, 0, ctypes.byref(h)) == did.DID_EINVAL
     assert did._lib.did_create(x, 0, 4, 1, 0, ctypes.byref(h)) == did.DID_EINVAL
     assert not h.value
+
+
+# ---------------------------------------------- struct layouts and constants
+STRUCTS = ["did_options", "did_info", "did_request", "did_result", "did_server_stats_t"]
+
+
+def c_struct_layout(tmp_path, did):
+    """sizeof and field offsets of every public struct, as a C compiler lays
+    them out from include/did.h (host ABI)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "did.h"', "int main(void) {"]
+    for s in STRUCTS:
+        lines.append('  printf("%s sizeof %%zu\\n", sizeof(%s));' % (s, s))
+        for f, _ in getattr(did, s)._fields_:
+            lines.append('  printf("%s %s %%zu\\n", offsetof(%s, %s));' % (s, f, s, f))
+    lines.append("  return 0;\n}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    return {tuple(line.split()[:2]): int(line.split()[2]) for line in out.splitlines()}
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    import paper_1802_08938_gb300 as did
+    layout = c_struct_layout(tmp_path, did)
+    for s in STRUCTS:
+        cls = getattr(did, s)
+        assert layout[(s, "sizeof")] == ctypes.sizeof(cls), s
+        for f, _ in cls._fields_:
+            assert layout[(s, f)] == getattr(cls, f).offset, (s, f)
+    # every field the header declares is bound (none missing from the binding)
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "did.h")).read(), flags=re.S)
+    for s in STRUCTS:
+        body = re.search(r"typedef struct \{([^{}]*)\}\s*%s;" % s, text).group(1)
+        names = set()
+        for decl in body.split(";"):
+            decl = decl.strip()
+            if not decl:
+                continue
+            for part in decl.split(","):
+                names.add(re.findall(r"[A-Za-z_][A-Za-z0-9_]*", part)[-1])
+        assert names == {f for f, _ in getattr(did, s)._fields_}, s
+
+
+def test_constants_match_the_header():
+    import paper_1802_08938_gb300 as did
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "did.h")).read(), flags=re.S)
+    found = 0
+    for name, val in re.findall(r"#define\s+(DID_[A-Z0-9_]+)\s+(-?\d+)", text):
+        assert getattr(did, name) == int(val), name
+        found += 1
+    for body in re.findall(r"typedef enum \{(.*?)\}", text, flags=re.S):
+        for name, val in re.findall(r"(DID_[A-Z0-9_]+)\s*=\s*(-?\d+)", body):
+            assert getattr(did, name) == int(val), name
+            found += 1
+    assert found >= 20
