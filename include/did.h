@@ -103,8 +103,9 @@ typedef struct {
  * the c-pass and the end of the second grid wait.  Read with
  * did_get_phase_times; costs four 8-byte stores per k. */
 #define DID_FLAG_PHASE_TIMES 1
-/* did_options.flags: refresh a bfloat16 residual with the float32 SIMT pass
- * instead of the tensor-core BF16x3 pass (for comparisons). */
+/* did_options.flags: refresh R = X - B C with the float32 SIMT pass instead of
+ * the tensor-core pass (BF16x3 for a bfloat16 residual with K <= 128, TF32x3
+ * for a float32 one with K <= 64; larger K always takes the SIMT pass). */
 #define DID_FLAG_SIMT_REFRESH 2
 /* did_options.flags (DID_ORDER_DID_BATCHED only): run the sweep's float32
  * GEMMs through cuBLAS's float32 emulation on the bfloat16 tensor cores (each
@@ -216,10 +217,13 @@ did_status did_objective(did_ctx* ctx, double* obj);
 /* 1/2 ||R||_F^2 of the stored residual (the last trace value). */
 did_status did_residual_objective(did_ctx* ctx, double* obj);
 
-/* Recompute R = X - B C densely (Algorithm 3 recomputes e_j := x_j - B c_j).
- * FP32 residual: float32 SIMT pass.  BF16 residual with K <= 128: tensor-core
- * pass (tcgen05, three bfloat16 products Bh Ch + Bh Cl + Bl Ch with float32
- * accumulation); larger K or DID_FLAG_SIMT_REFRESH: the SIMT pass. */
+/* Recompute R = X - B C densely (Algorithm 3 recomputes e_j := x_j - B c_j)
+ * on the tensor cores (tcgen05, three products Bh Ch + Bh Cl + Bl Ch of split
+ * operands with float32 accumulation): bfloat16 halves for a BF16 residual
+ * with K <= 128, TF32 parts for an FP32 residual with K <= 64.  Larger K or
+ * DID_FLAG_SIMT_REFRESH: the float32 SIMT pass.  Returns DID_ETIMEOUT if a
+ * bounded device wait of the tensor-core pass ran out (R is then recomputed
+ * before the next sweep). */
 did_status did_refresh_residual(did_ctx* ctx);
 
 /* Copy B (M x K column-major) and C (K x N row-major) out; either pointer

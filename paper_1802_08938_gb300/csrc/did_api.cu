@@ -187,7 +187,7 @@ did_status refresh_tc(did_ctx* c, double* f) {
   did_status st;
   const int G = did::refresh_tc_grid();
   if (!c->tc_ws) {
-    st = dev_alloc(c, &p, did::refresh_tc_workspace_bytes((int)c->M, c->ld, c->N, c->K));
+    st = dev_alloc(c, &p, did::refresh_tc_workspace_bytes((int)c->M, c->ld, c->N, c->K, !c->bf16));
     if (st != DID_OK) return st;
     c->tc_ws = p;
     st = dev_alloc(c, &p, sizeof(double) * G);
@@ -203,7 +203,7 @@ did_status refresh_tc(did_ctx* c, double* f) {
   DID_CUDA(c, cudaEventRecord(c->ev0, c->stream));
   DID_CUDA(c, did::launch_refresh_tc(c->X, c->R, c->B, c->C, (int)c->M, c->ld, c->N, c->K, c->tc_ws, c->tc_part,
                                      c->tc_err, c->opt.timeout_ns ? c->opt.timeout_ns : kDefaultTimeoutNs,
-                                     c->stream));
+                                     c->stream, !c->bf16));
   DID_CUDA(c, cudaEventRecord(c->ev1, c->stream));
   DID_CUDA(c, cudaMemcpyAsync(part.data(), c->tc_part, sizeof(double) * G, cudaMemcpyDeviceToHost, c->stream));
   DID_CUDA(c, cudaMemcpyAsync(&herr, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -225,7 +225,7 @@ did_status refresh_tc(did_ctx* c, double* f) {
 did_status refresh(did_ctx* c) {
   double s[3];
   did_status st;
-  if (c->bf16 && did::refresh_tc_supported(c->K) && !(c->opt.flags & DID_FLAG_SIMT_REFRESH)) {
+  if (did::refresh_tc_supported(c->K, !c->bf16) && !(c->opt.flags & DID_FLAG_SIMT_REFRESH)) {
     double f = 0.0;
     st = refresh_tc(c, &f);
     if (st != DID_OK) return st;

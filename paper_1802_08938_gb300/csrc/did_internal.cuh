@@ -352,12 +352,14 @@ struct DenseArgs {
 int dense_grid();
 cudaError_t launch_dense(const DenseArgs& a, cudaStream_t s);
 
-// Tensor-core refresh (bfloat16 residual): R = X - B C with BF16x3 products.
-bool refresh_tc_supported(int K);
-size_t refresh_tc_workspace_bytes(int M, int ld, int64_t N, int K);
+// Tensor-core refresh R = X - B C: BF16x3 products for a bfloat16 residual
+// (K <= 128), TF32x3 for a float32 one (f32, K <= 64).
+bool refresh_tc_supported(int K, bool f32);
+size_t refresh_tc_workspace_bytes(int M, int ld, int64_t N, int K, bool f32);
 int refresh_tc_grid();
 cudaError_t launch_refresh_tc(const float* X, void* R, const float* B, const float* C, int M, int ld, int64_t N,
-                              int K, void* workspace, double* part, int* err, uint64_t timeout_ns, cudaStream_t s);
+                              int K, void* workspace, double* part, int* err, uint64_t timeout_ns, cudaStream_t s,
+                              bool f32);
 
 // Batched DID (Algorithm 3 with one reduction per sweep; cuBLAS GEMMs).
 struct BatchedState;

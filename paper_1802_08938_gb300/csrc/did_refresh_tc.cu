@@ -1,13 +1,17 @@
-// Dense refresh R = X - B C on the 5th-generation tensor cores (tcgen05),
-// for the bfloat16-residual mode.
+// Dense refresh R = X - B C on the 5th-generation tensor cores (tcgen05).
 //
 // Algorithm 3 recomputes the residual e_j := x_j - B c_j at the top of every
 // iteration; the sweep keeps R and updates it in place, so a periodic dense
-// refresh resets the drift of the bfloat16 roundings.  The product B C is a
-// rank-K contraction with K <= 128, done as three bfloat16 products with
-// float32 accumulation ("BF16x3"): with B = Bh + Bl and C = Ch + Cl split into
-// bfloat16 high and low parts, B C ~= Bh Ch + Bh Cl + Bl Ch (the dropped Bl Cl
-// term is ~2^-16 relative), far below the bfloat16 rounding of the stored R.
+// refresh resets the drift of its roundings.  The product B C is a rank-K
+// contraction, done as three products of split operands with float32
+// accumulation.  With B = Bh + Bl and C = Ch + Cl, B C ~= Bh Ch + Bh Cl + Bl Ch:
+//   bfloat16 residual ("BF16x3", kind::f16, K <= 128): bfloat16 halves; the
+//     dropped Bl Cl term is ~2^-16 relative, far below the bfloat16 rounding of
+//     the stored R;
+//   float32 residual ("TF32x3", kind::tf32, K <= 64): Bh is the operand
+//     rounded to TF32's 11 significand bits, Bl = B - Bh (exact in float32,
+//     read by the tensor core as TF32); the error is ~2^-21 relative to
+//     |B||C| per product, of either sign.
 //
 // Kernel structure (one CTA per SM, persistent over 64-column tiles):
 //   warp 0      producer: TMA bulk copies of the C-factor tile (once per
@@ -20,9 +24,10 @@
 //               the sum of R^2 accumulated in float64.
 // Operands live in global memory pre-split and pre-tiled in the no-swizzle
 // K-major core-matrix layout (8 rows x 16 bytes per core matrix, core matrices
-// along K 128 bytes apart, along M/N Kp*16 bytes apart), so each operand tile
-// is one contiguous bulk copy and its shared-memory descriptor is a plain
-// (start, LBO = 128, SBO = Kp*16) triple.
+// along K 128 bytes apart, along M/N Kp*E*8 bytes apart for E-byte elements),
+// so each operand tile is one contiguous bulk copy and its shared-memory
+// descriptor is a plain (start, LBO = 128, SBO = Kp*E*8) triple.  One MMA
+// consumes 32 bytes of K (16 bfloat16 or 8 TF32 elements).
 //
 // Every mbarrier wait is bounded; on expiry the kernel records the error,
 // stops issuing work, waits (bounded) for its copies and MMAs, frees its
@@ -38,14 +43,15 @@ namespace {
 constexpr int kTcThreads = 256;     // 8 warps
 constexpr int kTileM = 128;         // rows per MMA (TMEM lanes)
 constexpr int kTileN = 64;          // columns per tile (MMA N)
-constexpr int kMaxKp = 128;         // K padded to a multiple of 16, at most 128
+constexpr int kMaxKp = 128;         // K padded to a multiple of 16, at most 128 (bfloat16)
+constexpr int kMaxKpTf32 = 64;      // TF32 operands take twice the shared memory
 constexpr int kTmemCols = 128;      // two accumulators of kTileN columns
 
 struct TcArgs {
   const float* X;            // ld x N float32, column-major
-  __nv_bfloat16* R;          // ld x N bfloat16 output
-  const __nv_bfloat16* Ahl;  // [row blocks][2][128 rows x Kp] tiled B factor (hi, lo)
-  const __nv_bfloat16* Bhl;  // [col tiles][2][64 cols x Kp] tiled C factor (hi, lo)
+  void* R;                   // ld x N output (bfloat16 or float32)
+  const void* Ahl;           // [row blocks][2][128 rows x Kp] tiled B factor (hi, lo)
+  const void* Bhl;           // [col tiles][2][64 cols x Kp] tiled C factor (hi, lo)
   double* part;              // [grid] sum of R^2 per CTA
   int* err;                  // error word
   int M, ld, Kp;
@@ -75,6 +81,10 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
 __host__ __device__ constexpr uint32_t instr_desc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+// kind::tf32: the same fields with A and B of format TF32 (value 2).
+__host__ __device__ constexpr uint32_t instr_desc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
 
 // -------------------------------------------------------------- tcgen05 ops
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
@@ -92,6 +102,15 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
@@ -125,11 +144,11 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, int* err
 struct TcSmem {
   size_t A, B, X, bars, tmem_slot, red, steps, total;
 };
-__host__ __device__ __forceinline__ TcSmem tc_smem(int Kp) {
+__host__ __device__ __forceinline__ TcSmem tc_smem(int Kp, int E) {
   TcSmem L;
   size_t o = 0;
-  L.A = o;    o += (size_t)2 * kTileM * Kp * 2;          // Bh, Bl row block
-  L.B = o;    o += (size_t)2 * kTileN * Kp * 2;          // Ch, Cl column tile
+  L.A = o;    o += (size_t)2 * kTileM * Kp * E;          // Bh, Bl row block
+  L.B = o;    o += (size_t)2 * kTileN * Kp * E;          // Ch, Cl column tile
   L.X = o;    o += (size_t)2 * kTileN * kTileM * 4;      // two X tiles [64 cols][128 rows]
   L.bars = o; o += 16 * sizeof(uint64_t);
   L.tmem_slot = o; o += 16;
@@ -151,9 +170,13 @@ enum {
   BAR_COUNT = 11
 };
 
+// F32: TF32x3 operands and a float32 residual; otherwise BF16x3 and bfloat16.
+template <bool F32>
 __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a) {
+  constexpr int E = F32 ? 4 : 2;                  // operand element bytes
+  constexpr int KSTEP = F32 ? 8 : 16;             // K per MMA (32 bytes)
   extern __shared__ __align__(1024) unsigned char sm[];
-  const TcSmem L = tc_smem(a.Kp);
+  const TcSmem L = tc_smem(a.Kp, E);
   unsigned char* sA = sm + L.A;
   unsigned char* sB = sm + L.B;
   float* sX = reinterpret_cast<float*>(sm + L.X);
@@ -164,10 +187,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a) {
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int Kp = a.Kp;
-  const uint32_t a_bytes = 2u * kTileM * Kp * 2;
-  const uint32_t b_bytes = 2u * kTileN * Kp * 2;
-  const uint32_t a_split = (uint32_t)kTileM * Kp * 2;     // bytes of one split of the A tile
-  const uint32_t b_split = (uint32_t)kTileN * Kp * 2;
+  const uint32_t a_bytes = 2u * kTileM * Kp * E;
+  const uint32_t b_bytes = 2u * kTileN * Kp * E;
+  const uint32_t a_split = (uint32_t)kTileM * Kp * E;     // bytes of one split of the A tile
+  const uint32_t b_split = (uint32_t)kTileN * Kp * E;
 
   if (threadIdx.x == 0) {
     *mma_steps = 0;
@@ -226,9 +249,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a) {
   } else if (warp == 1) {
     // ----------------------------------------------------------- MMA issue
     if (lane == 0) {
-      const uint32_t idesc = instr_desc_bf16(kTileM, kTileN);
+      const uint32_t idesc = F32 ? instr_desc_tf32(kTileM, kTileN) : instr_desc_bf16(kTileM, kTileN);
       const uint32_t sA0 = smem_u32(sA), sB0 = smem_u32(sB);
-      const uint32_t sbo = (uint32_t)Kp * 16;   // next 8-row group
+      const uint32_t sbo = (uint32_t)Kp * E * 8;   // next 8-row group
       for (int64_t s = 0; s < nsteps; ++s) {
         const int rb = (int)(s % a.row_blocks);
         const int64_t ti = s / a.row_blocks;
@@ -243,10 +266,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a) {
         for (int prod = 0; prod < 3; ++prod) {
           const uint32_t aoff = prod == 2 ? a_split : 0u;
           const uint32_t boff = prod == 1 ? b_split : 0u;
-          for (int kk = 0; kk < Kp / 16; ++kk) {
+          for (int kk = 0; kk < Kp / KSTEP; ++kk) {
             const uint64_t ad = smem_desc(sA0 + aoff + (uint32_t)kk * 256u, 128u, sbo);
             const uint64_t bd = smem_desc(sB0 + boff + (uint32_t)kk * 256u, 128u, sbo);
-            mma_bf16(d, ad, bd, idesc, acc);
+            if (F32)
+              mma_tf32(d, ad, bd, idesc, acc);
+            else
+              mma_bf16(d, ad, bd, idesc, acc);
             acc = 1;
           }
         }
@@ -282,15 +308,27 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a) {
       const int ncol = a.N - j0 < kTileN ? (int)(a.N - j0) : kTileN;
       float s2 = 0.f;
       if (ok && i < a.ld) {
-        __nv_bfloat16* rp = a.R + (size_t)j0 * a.ld + i;
+        if (F32) {
+          float* rp = static_cast<float*>(a.R) + (size_t)j0 * a.ld + i;
 #pragma unroll
-        for (int c = 0; c < kTileN; ++c) {
-          if (c < ncol) {
-            const float r = xs[c * kTileM] - d[c];
-            const __nv_bfloat16 rb16 = __float2bfloat16_rn(r);
-            rp[(size_t)c * a.ld] = rb16;
-            const float rr = __bfloat162float(rb16);
-            s2 = fmaf(rr, rr, s2);
+          for (int c = 0; c < kTileN; ++c) {
+            if (c < ncol) {
+              const float r = xs[c * kTileM] - d[c];
+              rp[(size_t)c * a.ld] = r;
+              s2 = fmaf(r, r, s2);
+            }
+          }
+        } else {
+          __nv_bfloat16* rp = static_cast<__nv_bfloat16*>(a.R) + (size_t)j0 * a.ld + i;
+#pragma unroll
+          for (int c = 0; c < kTileN; ++c) {
+            if (c < ncol) {
+              const float r = xs[c * kTileM] - d[c];
+              const __nv_bfloat16 rb16 = __float2bfloat16_rn(r);
+              rp[(size_t)c * a.ld] = rb16;
+              const float rr = __bfloat162float(rb16);
+              s2 = fmaf(rr, rr, s2);
+            }
           }
         }
       }
@@ -319,14 +357,41 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a) {
 }
 
 // ------------------------------------------------------------ operand prep
-// Tiled no-swizzle K-major layout of one split of a tile of `rows` rows:
-// element (r, k) at byte ((r/8) * (Kp/8) + k/8) * 128 + (r%8) * 16 + (k%8) * 2.
+// Tiled no-swizzle K-major layout of one split of a tile of `rows` rows, for
+// E-byte elements: element (r, k) at byte
+//   ((r/8) * (Kp*E/16) + (k*E)/16) * 128 + (r%8) * 16 + (k*E) % 16.
+template <int E>
 __device__ __forceinline__ size_t tiled_index(int r, int k, int Kp) {
-  return ((size_t)(r >> 3) * (Kp >> 3) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7);   // in elements
+  constexpr int per16 = 16 / E;                  // elements per 16-byte core-matrix row
+  return ((size_t)(r >> 3) * (Kp / per16) + (k / per16)) * (8 * per16) + (r & 7) * per16 + (k % per16);
 }
 
+// Split of v into a high part and a remainder: bfloat16 halves (round to
+// nearest), or for TF32 the value rounded to its top 11 significand bits
+// (nearest, ties away from zero: add half a TF32 ulp to the magnitude bits,
+// clear the 13 low bits; a carry into the exponent is the correct rounding)
+// and the exact float32 remainder, signed and at most half a TF32 ulp.
+// Truncating instead would bias every remainder towards the operand's sign.
+template <typename T>
+struct Split;
+template <>
+struct Split<__nv_bfloat16> {
+  static __device__ __forceinline__ void run(float v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+    hi = __float2bfloat16_rn(v);
+    lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+  }
+};
+template <>
+struct Split<float> {
+  static __device__ __forceinline__ void run(float v, float& hi, float& lo) {
+    hi = __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xFFFFE000u);
+    lo = v - hi;
+  }
+};
+
 // B factor (ld x K column-major float32) -> [row block][split][128 x Kp].
-__global__ void prep_b_kernel(const float* B, int M, int ld, int K, int Kp, int row_blocks, __nv_bfloat16* out) {
+template <typename T>
+__global__ void prep_b_kernel(const float* B, int M, int ld, int K, int Kp, int row_blocks, T* out) {
   const int64_t n = (int64_t)row_blocks * kTileM * Kp;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
        idx += (int64_t)gridDim.x * blockDim.x) {
@@ -334,16 +399,17 @@ __global__ void prep_b_kernel(const float* B, int M, int ld, int K, int Kp, int 
     const int64_t rg = idx / Kp;                 // global row
     const int rb = (int)(rg / kTileM), r = (int)(rg % kTileM);
     const float v = (rg < M && k < K) ? B[(size_t)k * ld + rg] : 0.f;
-    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-    const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-    __nv_bfloat16* base = out + (size_t)rb * 2 * kTileM * Kp;
-    base[tiled_index(r, k, Kp)] = hi;
-    base[(size_t)kTileM * Kp + tiled_index(r, k, Kp)] = lo;
+    T hi, lo;
+    Split<T>::run(v, hi, lo);
+    T* base = out + (size_t)rb * 2 * kTileM * Kp;
+    base[tiled_index<sizeof(T)>(r, k, Kp)] = hi;
+    base[(size_t)kTileM * Kp + tiled_index<sizeof(T)>(r, k, Kp)] = lo;
   }
 }
 
 // C factor (K x N row-major float32) -> [column tile][split][64 x Kp].
-__global__ void prep_c_kernel(const float* C, int64_t N, int K, int Kp, int64_t col_tiles, __nv_bfloat16* out) {
+template <typename T>
+__global__ void prep_c_kernel(const float* C, int64_t N, int K, int Kp, int64_t col_tiles, T* out) {
   const int64_t n = col_tiles * kTileN * Kp;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
        idx += (int64_t)gridDim.x * blockDim.x) {
@@ -352,11 +418,11 @@ __global__ void prep_c_kernel(const float* C, int64_t N, int K, int Kp, int64_t 
     const int64_t ct = cg / kTileN;
     const int c = (int)(cg % kTileN);
     const float v = (cg < N && k < K) ? C[(size_t)k * N + cg] : 0.f;
-    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-    const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-    __nv_bfloat16* base = out + (size_t)ct * 2 * kTileN * Kp;
-    base[tiled_index(c, k, Kp)] = hi;
-    base[(size_t)kTileN * Kp + tiled_index(c, k, Kp)] = lo;
+    T hi, lo;
+    Split<T>::run(v, hi, lo);
+    T* base = out + (size_t)ct * 2 * kTileN * Kp;
+    base[tiled_index<sizeof(T)>(c, k, Kp)] = hi;
+    base[(size_t)kTileN * Kp + tiled_index<sizeof(T)>(c, k, Kp)] = lo;
   }
 }
 
@@ -369,33 +435,35 @@ int sm_count_tc() {
 
 }  // namespace
 
-bool refresh_tc_supported(int K) { return K >= 1 && K <= kMaxKp; }
+bool refresh_tc_supported(int K, bool f32) { return K >= 1 && K <= (f32 ? kMaxKpTf32 : kMaxKp); }
 
-size_t refresh_tc_workspace_bytes(int M, int ld, int64_t N, int K) {
+size_t refresh_tc_workspace_bytes(int M, int ld, int64_t N, int K, bool f32) {
   const int Kp = (K + 15) / 16 * 16;
+  const int E = f32 ? 4 : 2;
   const int row_blocks = (ld + kTileM - 1) / kTileM;
   const int64_t col_tiles = (N + kTileN - 1) / kTileN;
   (void)M;
-  return (size_t)row_blocks * 2 * kTileM * Kp * 2 + (size_t)col_tiles * 2 * kTileN * Kp * 2;
+  return (size_t)row_blocks * 2 * kTileM * Kp * E + (size_t)col_tiles * 2 * kTileN * Kp * E;
 }
 
 int refresh_tc_grid() { return sm_count_tc(); }
 
-cudaError_t launch_refresh_tc(const float* X, void* R, const float* B, const float* C, int M, int ld, int64_t N, int K,
-                              void* workspace, double* part, int* err, uint64_t timeout_ns, cudaStream_t s) {
+template <typename T, bool F32>
+static cudaError_t launch_tc(const float* X, void* R, const float* B, const float* C, int M, int ld, int64_t N,
+                             int K, void* workspace, double* part, int* err, uint64_t timeout_ns, cudaStream_t s) {
   const int Kp = (K + 15) / 16 * 16;
   const int row_blocks = (ld + kTileM - 1) / kTileM;
   const int64_t col_tiles = (N + kTileN - 1) / kTileN;
-  __nv_bfloat16* Ahl = static_cast<__nv_bfloat16*>(workspace);
-  __nv_bfloat16* Bhl = Ahl + (size_t)row_blocks * 2 * kTileM * Kp;
+  T* Ahl = static_cast<T*>(workspace);
+  T* Bhl = Ahl + (size_t)row_blocks * 2 * kTileM * Kp;
   const int sms = sm_count_tc();
-  prep_b_kernel<<<sms * 4, 256, 0, s>>>(B, M, ld, K, Kp, row_blocks, Ahl);
-  prep_c_kernel<<<sms * 8, 256, 0, s>>>(C, N, K, Kp, col_tiles, Bhl);
+  prep_b_kernel<T><<<sms * 4, 256, 0, s>>>(B, M, ld, K, Kp, row_blocks, Ahl);
+  prep_c_kernel<T><<<sms * 8, 256, 0, s>>>(C, N, K, Kp, col_tiles, Bhl);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   TcArgs a{};
   a.X = X;
-  a.R = static_cast<__nv_bfloat16*>(R);
+  a.R = R;
   a.Ahl = Ahl;
   a.Bhl = Bhl;
   a.part = part;
@@ -407,11 +475,19 @@ cudaError_t launch_refresh_tc(const float* X, void* R, const float* B, const flo
   a.row_blocks = row_blocks;
   a.col_tiles = col_tiles;
   a.timeout_ns = timeout_ns;
-  const size_t smem = tc_smem(Kp).total;
-  e = cudaFuncSetAttribute(refresh_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = tc_smem(Kp, (int)sizeof(T)).total;
+  e = cudaFuncSetAttribute(refresh_tc_kernel<F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  refresh_tc_kernel<<<sms, kTcThreads, smem, s>>>(a);
+  refresh_tc_kernel<F32><<<sms, kTcThreads, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+cudaError_t launch_refresh_tc(const float* X, void* R, const float* B, const float* C, int M, int ld, int64_t N, int K,
+                              void* workspace, double* part, int* err, uint64_t timeout_ns, cudaStream_t s,
+                              bool f32) {
+  if (!refresh_tc_supported(K, f32)) return cudaErrorInvalidValue;
+  return f32 ? launch_tc<float, true>(X, R, B, C, M, ld, N, K, workspace, part, err, timeout_ns, s)
+             : launch_tc<__nv_bfloat16, false>(X, R, B, C, M, ld, N, K, workspace, part, err, timeout_ns, s);
 }
 
 }  // namespace did

@@ -1,4 +1,4 @@
-"""Tensor-core refresh (tcgen05, BF16x3) of a bfloat16 residual.
+"""Tensor-core refresh (tcgen05): BF16x3 for a bfloat16 residual, TF32x3 for a float32 one.
 
 R = X - B C from three bfloat16 products with float32 accumulation must equal
 the exact X - B C up to (a) the dropped Bl Cl term and the float32
@@ -70,3 +70,64 @@ def test_tensor_core_refresh_in_a_bf16_run(did):
     print("BF16-R 10 sweeps: f(tc refresh)=%.8g f(simt refresh)=%.8g, tc refreshes %d" % (f_tc, f_simt, n_tc))
     assert n_tc == 5 and n_simt == 0
     assert abs(f_tc - f_simt) <= 1e-3 * f_simt
+
+
+# ------------------------------------------------- TF32x3 (float32 residual)
+@pytest.mark.parametrize("M,N,K", [(200, 1000, 10), (517, 777, 64), (128, 64, 16), (5000, 2100, 50), (129, 130, 64),
+                                   (300, 500, 3)])
+def test_tensor_core_refresh_fp32_matches_product(did, M, N, K):
+    """TF32x3: Bh Ch + Bh Cl + Bl Ch with Bh the operand rounded to 11
+    significand bits; the remainders are read as TF32 (11 bits), so a product
+    is off by about 2^-21 relative, plus float32 accumulation over Kp terms."""
+    X, _, _ = W.planted(M, N, K, seed=2 * M + N, sigma=0.01)
+    B0, C0 = W.init_factors(M, N, K, 9)
+    Xc = np.ascontiguousarray(X.T)
+    kw = dict(B_init=np.ascontiguousarray(B0.T), C_init=C0)
+    with did.Context(Xc, M, N, K, **kw) as tc, did.Context(Xc, M, N, K, flags=did.DID_FLAG_SIMT_REFRESH, **kw) as simt:
+        info = tc.info()
+        R_tc = tc.residual().astype(np.float64)
+        R_simt = simt.residual().astype(np.float64)
+        f_tc, f_simt = tc.trace()[0], simt.trace()[0]
+        assert simt.info()["tc_refreshes"] == 0
+    assert info["tc_refreshes"] == 1
+    absP = np.abs(B0).astype(np.float64) @ np.abs(C0).astype(np.float64)
+    R_exact = X.astype(np.float64) - B0.astype(np.float64) @ C0.astype(np.float64)
+    bound = 2.0 ** -17 * absP + 2.0 ** -22 * np.abs(R_exact)
+    err = np.abs(R_tc - R_exact)
+    print("TF32x3 M=%d N=%d K=%d: max err/|BC| %.3g, max err/bound %.3g, SIMT max err/|BC| %.3g, f rel %.3g"
+          % (M, N, K, (err / absP).max(), (err / bound).max(), (np.abs(R_simt - R_exact) / absP).max(),
+             abs(f_tc - f_simt) / f_simt))
+    assert np.all(err <= bound)
+    # the objective of the refreshed residual, from the elementwise bound
+    f_exact = 0.5 * float(np.sum(R_exact ** 2))
+    assert abs(f_tc - f_exact) <= float(np.sum(bound * (np.abs(R_exact) + 0.5 * bound)))
+    assert abs(f_tc - f_simt) <= 1e-5 * f_simt      # the FP32 objective tolerance
+
+
+def test_fp32_refresh_above_k64_is_simt(did):
+    M, N, K = 300, 400, 100
+    X, _, _ = W.planted(M, N, K, seed=5, sigma=0.01)
+    with did.Context(np.ascontiguousarray(X.T), M, N, K, seed=5) as ctx:
+        assert ctx.info()["tc_refreshes"] == 0
+
+
+def test_tensor_core_refresh_in_an_fp32_run(did):
+    """An FP32 run refreshing every 2 sweeps on the tensor cores stays within
+    the FP32 parity tolerances of the oracle (refreshes do not change the
+    iterates in exact arithmetic)."""
+    from oracle import did_oracle as O
+    M, N, K = 600, 4000, 24
+    X, _, _ = W.planted(M, N, K, seed=3, sigma=0.01)
+    B0, C0 = W.init_factors(M, N, K, 3)
+    ref = O.factor(X, B0, C0, order="hals", max_iter=20, stop="none")
+    with did.Context(np.ascontiguousarray(X.T), M, N, K, B_init=np.ascontiguousarray(B0.T), C_init=C0,
+                     refresh_every=2) as ctx:
+        ctx.sweep(20)
+        B, C = ctx.factors()
+        t = ctx.trace()
+        n_tc = ctx.info()["tc_refreshes"]
+    eB = np.linalg.norm(B - ref["B"]) / np.linalg.norm(ref["B"])
+    eF = float(np.max(np.abs(t - ref["trace"]) / ref["trace"]))
+    print("FP32 20 sweeps, TF32x3 refresh every 2: tc refreshes %d, relB %.3g, max relf %.3g" % (n_tc, eB, eF))
+    assert n_tc == 10
+    assert eB <= 1e-4 and eF <= 1e-5
