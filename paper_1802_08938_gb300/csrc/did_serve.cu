@@ -281,6 +281,7 @@ bool run_round(did_server* s, std::vector<Req*>& act) {
     a.tol = r->rq.tol;
     a.order = DID_ORDER_INTERLEAVED;
     a.timeout_ns = kServeTimeoutNs;
+    a.pair = plan.pair;
     a.cta_begin = begin;
     a.cta_count = sh[i];
     begin += sh[i];

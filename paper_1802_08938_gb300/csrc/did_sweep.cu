@@ -175,7 +175,7 @@ did_status plan_instance(int ld, int64_t N, bool bf16, int ncta, size_t smem_bud
     if (sweep_smem(ld, plan->NG, D, elem, false).total <= smem_budget) { plan->D = D; break; }
   if (plan->D == 0) return DID_E_TOO_LARGE;
   plan->lazy = 0;
-  plan->pair = 0;
+  plan->pair = kServePairs && plan->D >= 4 ? 1 : 0;
   plan->smem = sweep_smem(ld, plan->NG, plan->D, elem, false).total;
   plan->grid = ncta;
   plan->func = serve_func(bf16);

@@ -52,6 +52,10 @@ constexpr int kMaxStages = DID_MAX_STAGES;   // ring stages per column group (up
 #define DID_PAIRS 1
 #endif
 constexpr bool kPairs = DID_PAIRS != 0;      // c-passes may take columns in pairs
+#ifndef DID_SERVE_PAIRS
+#define DID_SERVE_PAIRS 1
+#endif
+constexpr bool kServePairs = DID_SERVE_PAIRS != 0;   // serving instances too
 
 // Sum v over the GS threads of a column group; every thread of the group gets
 // the same value (xor tree within warps, then the warps' totals in order).
@@ -908,8 +912,9 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a, int cta, int ncta
       const float beta_o = lz == 2 ? (float)bc[0] : 0.f, beta_n = lz == 2 ? (float)bc[3] : 0.f;
       const bool last = k == a.K - 1;
       // Pairs pay off where a pass is bound by per-column work: a bfloat16
-      // residual, and the deferred (read-only) pass of a float32 one.
-      if (!GEN && a.pair && (BF16 || lz == 1)) {
+      // residual, the deferred (read-only) pass of a float32 one, and the
+      // short columns of the serving instances.
+      if (a.pair && (BF16 || GEN || lz == 1)) {
         if (lz == 2) {
           if (last)
             column_pass<NR, BF16, kUpdateC, true, GEN, 2, 2>(a, cta, k, knext, inv_bb, alpha, cdeg, sm, it, pass++,
