@@ -38,6 +38,7 @@ struct did_ctx {
   double* OBJp = nullptr;
   float* bold = nullptr;
   float* Cold = nullptr;            // c_k before a deferred pass (lazy write-back), N floats
+  double* XCp = nullptr;            // deferred passes: per-unit sums of c_k c_{k+1} before/after
   Ctrl* ctrl = nullptr;
   double* trace_dev = nullptr;
   unsigned long long* degen = nullptr;
@@ -258,6 +259,7 @@ did_status launch_sweeps(did_ctx* c, int n, int stop_rule, double tol, int* done
   a.bold = c->bold;
   a.lazy = c->plan.lazy;
   a.Cold = c->Cold;
+  a.XCp = c->XCp;
   a.pair = c->opt.order == DID_ORDER_INTERLEAVED && !(c->opt.flags & DID_FLAG_SINGLE_COLUMNS) ? c->plan.pair : 0;
   a.ctrl = c->ctrl;
   a.trace = c->trace_dev;
@@ -465,7 +467,10 @@ static did_status create_impl(did_ctx* c, const float* X, uint64_t seed) {
   ALLOC(Sp, (size_t)2 * G * sizeof(double));
   ALLOC(OBJp, U * sizeof(double));
   ALLOC(bold, (size_t)c->ld * sizeof(float));
-  if (c->plan.lazy) ALLOC(Cold, (size_t)N * sizeof(float));
+  if (c->plan.lazy) {
+    ALLOC(Cold, (size_t)N * sizeof(float));
+    ALLOC(XCp, 2 * U * sizeof(double));
+  }
   ALLOC(ctrl, sizeof(Ctrl));
   ALLOC(trace_dev, sizeof(double) * kMaxSweepsPerLaunch);
   ALLOC(degen, sizeof(unsigned long long));

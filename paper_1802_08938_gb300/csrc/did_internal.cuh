@@ -309,6 +309,8 @@ struct SweepArgs {
   int lazy;           // 1: deferred write-back in pairs of k (interleaved order)
   float* Cold;        // [N] c_k before a deferred pass (lazy only)
   int pair;           // 1: column groups take two columns per iteration (needs D >= 4)
+  double* XCp;        // [npart][2] per-unit sums of c_k c_{k+1} before and after
+                      // the update of c_k (deferred passes; lazy only)
 };
 
 struct SweepPlan {

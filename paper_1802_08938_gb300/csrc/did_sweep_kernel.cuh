@@ -125,7 +125,7 @@ __host__ __device__ __forceinline__ SweepSmem sweep_smem(int ld, int NG, int D, 
   L.red = o;  o += 512 * sizeof(float);
   L.redd = o; o += 16 * 16 * sizeof(double);
   L.dscr = o; o += kWarps * sizeof(double);
-  L.bc = o;   o += 4 * sizeof(double);
+  L.bc = o;   o += 8 * sizeof(double);
   L.meta = o; o += (size_t)NG * D * sizeof(int64_t);
   L.mbar = o; o += (size_t)NG * D * sizeof(uint64_t);
   L.total = o;
@@ -160,8 +160,11 @@ struct SmemPtrs {
 // the stages this group has consumed since the launch (stage and phase).
 // Vector slots r < NR-1 are always inside the column (NR = ceil(nvec / GS));
 // only the last slot needs a bounds test.
-// LZ (kUpdateC only): 0 plain; 1 deferred -- no store of R, c_k before the
-// update saved to a.Cold; 2 applying -- the column read is R without the
+// LZ (kUpdateC only): 0 plain; 1 deferred -- no store of R and no update of
+// the column: the partials of R' c_knext^T are formed from the stored column,
+// and the b-reduce that follows adds the pending change as b_k (c_k.c_knext)
+// - b_k' (c_k'.c_knext), from the per-unit sums a.XCp; c_k before the update
+// is saved to a.Cold; 2 applying -- the column read is R without the
 // pending change b_{k-1} c_{k-1} - b_{k-1}' c_{k-1}' (pbo, pbn, a.Cold and C
 // row k-1), which the dot takes as beta_o c_old - beta_n c_new (beta_o =
 // b_k'.b_{k-1}, beta_n = b_k'.b_{k-1}') and the update adds before storing.
@@ -244,6 +247,7 @@ __device__ __forceinline__ void column_pass(const SweepArgs& a, int cta, int k, 
     hi = make_float2(t.z, t.w);
   };
   double cc_acc = 0.0, obj_acc = 0.0;
+  double xo_acc = 0.0, xn_acc = 0.0;   // deferred pass: sum c_old c_next, sum c_new c_next
   int parity = 0;
 
   // Producer state (used by the group's first thread only).
@@ -306,6 +310,13 @@ __device__ __forceinline__ void column_pass(const SweepArgs& a, int cta, int k, 
     }
     if (lt == 0) __stcg(a.CCp + u, cc_acc);
     cc_acc = 0.0;
+    if (LZ == 1) {
+      if (lt == 0) {
+        __stcg(a.XCp + 2 * u, xo_acc);
+        __stcg(a.XCp + 2 * u + 1, xn_acc);
+      }
+      xo_acc = xn_acc = 0.0;
+    }
     if (OBJ) {
       const double o = group_sum_f64(obj_acc, GS, g, lt, sm.redd);
       if (lt == 0) __stcg(a.OBJp + u, o);
@@ -385,6 +396,57 @@ __device__ __forceinline__ void column_pass(const SweepArgs& a, int cta, int k, 
       raw* Rcol1 = reinterpret_cast<raw*>(a.R) + (two ? jj[1] : jj[0]) * nvec + lt;
 
       float cnew[2] = {co[0], co[1]};
+      if (MODE == kUpdateC && LZ == 1) {
+        // Deferred pass (see the one-column loop): one read per stage, the
+        // consumed stages refilled right after the group barrier.
+        float2 da = make_float2(0.f, 0.f), db = make_float2(0.f, 0.f);
+        const float2 x0 = make_float2(cx[0], cx[0]), x1 = make_float2(cx[1], cx[1]);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          if (slot_ok(r)) {
+            float f0[VR], f1[VR];
+            V::unpack(stage0[r * GS], f0);
+            V::unpack(stage1[r * GS], f1);
+#pragma unroll
+            for (int e = 0; e < VR; e += 4) {
+              float2 blo, bhi;
+              bn_quad(r, e, blo, bhi);
+              da = __ffma2_rn(blo, make_float2(f0[e], f0[e + 1]), da);
+              da = __ffma2_rn(bhi, make_float2(f0[e + 2], f0[e + 3]), da);
+              db = __ffma2_rn(blo, make_float2(f1[e], f1[e + 1]), db);
+              db = __ffma2_rn(bhi, make_float2(f1[e + 2], f1[e + 3]), db);
+            }
+#pragma unroll
+            for (int h = 0; h < VH; ++h) {
+              p[r][h] = __ffma2_rn(make_float2(f0[2 * h], f0[2 * h + 1]), x0, p[r][h]);
+              if (two) p[r][h] = __ffma2_rn(make_float2(f1[2 * h], f1[2 * h + 1]), x1, p[r][h]);
+            }
+          }
+        }
+        const float2 dot2 = group_sum2(make_float2(da.x + da.y, db.x + db.y), GS, g, lt, sm.red, parity);
+        parity ^= 1;
+        if (lt == 0) {                      // nothing is pending: this pass refills at once
+          fence_proxy_async_shared();
+          issue(sts[0]);
+          if (two) issue(sts[1]);
+        }
+        const float dots[2] = {dot2.x, dot2.y};
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          if (!cdeg) {
+            const float t = fmaf(alpha, co[c], dots[c] * inv_bb);
+            cnew[c] = t > 0.f ? t : 0.f;
+          }
+          if (lt == 0 && (c == 0 || two)) {
+            __stcg(Cw + jj[c], cnew[c]);
+            __stcg(a.Cold + jj[c], co[c]);
+            cc_acc += (double)cx[c] * (double)cx[c];
+            xo_acc += (double)co[c] * (double)cx[c];
+            xn_acc += (double)cnew[c] * (double)cx[c];
+          }
+        }
+        continue;
+      }
       if (MODE == kUpdateC) {
         float2 da = make_float2(0.f, 0.f), db = make_float2(0.f, 0.f);
 #pragma unroll
@@ -444,7 +506,7 @@ __device__ __forceinline__ void column_pass(const SweepArgs& a, int cta, int k, 
           float f0[VR], f1[VR];
           V::unpack(stage0[r * GS], f0);
           V::unpack(stage1[r * GS], f1);
-          if (MODE != kPrologue) {
+          if (MODE != kPrologue && LZ != 1) {
 #pragma unroll
             for (int e = 0; e < VR; e += 4) {
               const int bi = BF16 ? (e / 4) * half + q * 4 : q * VR + e;
@@ -476,10 +538,8 @@ __device__ __forceinline__ void column_pass(const SweepArgs& a, int cta, int k, 
                 f[e] = lo.x; f[e + 1] = lo.y; f[e + 2] = hi.x; f[e + 3] = hi.y;
               }
             }
-            if (LZ != 1) {
-              __stcs(Rcol0 + r * GS, V::pack(f0));
-              if (two) __stcs(Rcol1 + r * GS, V::pack(f1));
-            }
+            __stcs(Rcol0 + r * GS, V::pack(f0));
+            if (two) __stcs(Rcol1 + r * GS, V::pack(f1));
           }
           const float2 n0 = make_float2(cn[0], cn[0]), n1 = make_float2(cn[1], cn[1]);
 #pragma unroll
@@ -498,6 +558,14 @@ __device__ __forceinline__ void column_pass(const SweepArgs& a, int cta, int k, 
       if (lt == 0) {
         cc_acc += (double)cn[0] * (double)cn[0];
         if (two) cc_acc += (double)cn[1] * (double)cn[1];
+        if (LZ == 1) {
+          xo_acc += (double)co[0] * (double)cn[0];
+          xn_acc += (double)cnew[0] * (double)cn[0];
+          if (two) {
+            xo_acc += (double)co[1] * (double)cn[1];
+            xn_acc += (double)cnew[1] * (double)cn[1];
+          }
+        }
       }
       if (OBJ) {
         obj_acc += (double)(sa.x + sa.y);
@@ -550,6 +618,47 @@ __device__ __forceinline__ void column_pass(const SweepArgs& a, int cta, int k, 
     raw* Rcol = reinterpret_cast<raw*>(a.R) + j * nvec + lt;
 
     float c_new = c_old;
+    if (MODE == kUpdateC && LZ == 1) {
+      // Deferred pass: one read of the stage gives the dot and the partials of
+      // R_s c_knext^T; every thread of the group is then done with the stage,
+      // so it is refilled right after the group barrier.
+      float2 d2 = make_float2(0.f, 0.f);
+      const float2 cx2 = make_float2(c_nx, c_nx);
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        if (slot_ok(r)) {
+          float f[VR];
+          V::unpack(stage[r * GS], f);
+#pragma unroll
+          for (int e = 0; e < VR; e += 4) {
+            float2 blo, bhi;
+            bn_quad(r, e, blo, bhi);
+            d2 = __ffma2_rn(blo, make_float2(f[e], f[e + 1]), d2);
+            d2 = __ffma2_rn(bhi, make_float2(f[e + 2], f[e + 3]), d2);
+          }
+#pragma unroll
+          for (int h = 0; h < VH; ++h) p[r][h] = __ffma2_rn(make_float2(f[2 * h], f[2 * h + 1]), cx2, p[r][h]);
+        }
+      }
+      const float dot = group_sum(d2.x + d2.y, GS, g, lt, sm.red, parity);
+      parity ^= 1;
+      if (lt == 0) {
+        fence_proxy_async_shared();
+        issue(st);
+      }
+      if (!cdeg) {
+        const float t = fmaf(alpha, c_old, dot * inv_bb);
+        c_new = t > 0.f ? t : 0.f;
+      }
+      if (lt == 0) {
+        __stcg(Cw + j, c_new);
+        __stcg(a.Cold + j, c_old);
+        cc_acc += (double)c_nx * (double)c_nx;
+        xo_acc += (double)c_old * (double)c_nx;
+        xn_acc += (double)c_new * (double)c_nx;
+      }
+      continue;
+    }
     if (MODE == kUpdateC) {
       float2 d2 = make_float2(0.f, 0.f);
 #pragma unroll
@@ -597,7 +706,7 @@ __device__ __forceinline__ void column_pass(const SweepArgs& a, int cta, int k, 
         const int q = lt + r * GS;
         float f[VR];
         V::unpack(stage[r * GS], f);
-        if (MODE != kPrologue) {
+        if (MODE != kPrologue && LZ != 1) {
 #pragma unroll
           for (int e = 0; e < VR; e += 4) {
             // BF16: the 8 previous-b values of vector q are stored as two
@@ -622,7 +731,7 @@ __device__ __forceinline__ void column_pass(const SweepArgs& a, int cta, int k, 
             hi = __ffma2_rn(make_float2(t.z, t.w), co2, hi);
             f[e] = lo.x; f[e + 1] = lo.y; f[e + 2] = hi.x; f[e + 3] = hi.y;
           }
-          if (LZ != 1) __stcs(Rcol + r * GS, V::pack(f));
+          __stcs(Rcol + r * GS, V::pack(f));
         }
 #pragma unroll
         for (int h = 0; h < VH; ++h) {
@@ -632,7 +741,13 @@ __device__ __forceinline__ void column_pass(const SweepArgs& a, int cta, int k, 
         }
       }
     }
-    if (lt == 0) cc_acc += (double)cn * (double)cn;
+    if (lt == 0) {
+      cc_acc += (double)cn * (double)cn;
+      if (LZ == 1) {
+        xo_acc += (double)c_old * (double)cn;
+        xn_acc += (double)c_new * (double)cn;
+      }
+    }
     if (OBJ) obj_acc += (double)(s2.x + s2.y);
   }
   }   // NC == 1
@@ -664,6 +779,14 @@ __device__ __forceinline__ void column_pass(const SweepArgs& a, int cta, int k, 
     }
     const double cc = block_sum_f64(cc_acc, sm.dscr);
     if (threadIdx.x == 0) __stcg(a.CCp + cta, cc);
+    if (LZ == 1) {
+      const double xo = block_sum_f64(xo_acc, sm.dscr);
+      const double xn = block_sum_f64(xn_acc, sm.dscr);
+      if (threadIdx.x == 0) {
+        __stcg(a.XCp + 2 * cta, xo);
+        __stcg(a.XCp + 2 * cta + 1, xn);
+      }
+    }
     if (OBJ) {
       const double o = block_sum_f64(obj_acc, sm.dscr);
       if (threadIdx.x == 0) __stcg(a.OBJp + cta, o);
@@ -679,13 +802,25 @@ __device__ __forceinline__ void column_pass(const SweepArgs& a, int cta, int k, 
 // subset t / rows, up to 16 loads in flight); the subsets' sums are added in
 // subset order, then one thread per row forms b_k'.  With few partial rows
 // (an instance on few CTAs) a round covers up to 512 rows.
+// corr (the partials come from a deferred pass for k-1): s gains the pending
+// change of block k-1, b_{k-1} (c_{k-1}.c_k) - b_{k-1}' (c_{k-1}'.c_k), with
+// b_{k-1} from a.bold (read before this reduce overwrites it) and the two dot
+// products summed over a.XCp in float64.
 __device__ __forceinline__ void b_reduce(const SweepArgs& a, int cta, int G, int k, float* acc, double* bc,
-                                         double* dscr) {
+                                         double* dscr, bool corr = false) {
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   const int U = a.npart;
   if (w == 0) {
     const double cc = warp_sum_global_f64(a.CCp, U, 1);
     if (l == 0) bc[0] = cc;
+  }
+  if (corr && w == 1) {
+    const double so = warp_sum_global_f64(a.XCp, U, 2);
+    const double sn = warp_sum_global_f64(a.XCp + 1, U, 2);
+    if (l == 0) {
+      bc[4] = so;
+      bc[5] = sn;
+    }
   }
   const int rpc = (a.ld + G - 1) / G;
   const int r0 = cta * rpc;
@@ -721,9 +856,12 @@ __device__ __forceinline__ void b_reduce(const SweepArgs& a, int cta, int G, int
       float tot = 0.f;
       for (int sb = 0; sb < S; ++sb) tot += acc[sb * per_round + t];
       const float b_old = __ldcg(a.B + (size_t)k * a.ld + row);
+      double totd = (double)tot;
+      if (corr)   // the pending change of block k-1 (a.bold still holds b_{k-1} here)
+        totd += (double)__ldcg(a.bold + row) * bc[4] - (double)__ldcg(a.B + (size_t)(k - 1) * a.ld + row) * bc[5];
       float b_new = b_old;
       if (cc > 0.0) {
-        const double v = (double)b_old + (double)tot / cc;
+        const double v = (double)b_old + totd / cc;
         b_new = v > 0.0 ? (float)v : 0.f;
       }
       __stcg(a.bold + row, b_old);
@@ -891,7 +1029,8 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a, int cta, int ncta
       const int step = s * a.K + k;
       const bool rec = stamps && step < a.tstamp_cap;
       if (rec) a.tstamp[4 * step + 0] = globaltimer_ns();
-      b_reduce(a, cta, G, k, sm.red, bc, sm.dscr);
+      // after a deferred pass (k odd) the partials lack the pending change
+      b_reduce(a, cta, G, k, sm.red, bc, sm.dscr, lazy && (k & 1));
       DID_GRID_SYNC();
       if (rec) a.tstamp[4 * step + 1] = globaltimer_ns();
       if (w == 0) {
