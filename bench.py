@@ -135,10 +135,11 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------- CPU oracle
-def cpu_sample(workload, cols, sweeps):
+def cpu_sample(workload, cols, sweeps, threads=1):
     """Time `sweeps` oracle sweeps on the first `cols` columns (runs in a child
-    process with one BLAS thread).  Returns seconds per sweep of the slice."""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    process with `threads` BLAS threads).  Returns seconds per sweep of the slice."""
+    t = str(int(threads))
+    env = dict(os.environ, OMP_NUM_THREADS=t, OPENBLAS_NUM_THREADS=t, MKL_NUM_THREADS=t)
     code = ("import sys, json; sys.path.insert(0, %r); import bench; "
             "print(json.dumps(bench._cpu_sample_child(%r, %d, %d)))" % (ROOT, workload, cols, sweeps))
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, cwd=ROOT)
@@ -170,13 +171,22 @@ def _cpu_sample_child(workload, cols, sweeps):
 
 
 def cpu_baseline(workload):
+    """The FP64 oracle as it stands on the host cores: one thread (the
+    baseline), and all cores (BLAS threads; the oracle's elementwise NumPy
+    steps stay single-threaded)."""
     w = WORKLOADS[workload]
     cols = min(CPU_SAMPLE_COLS[workload], w["N"])
     r = cpu_sample(workload, cols, CPU_SAMPLE_SWEEPS)
     sweeps_per_s = (1.0 / r["sec_per_sweep"]) * cols / w["N"]
-    return {"value": sweeps_per_s, "unit": "sweeps/s", "cores": 1, "kind": "oracle",
-            "sample": "%d FP64 oracle sweeps (NumPy, 1 thread) on the first %d of %d columns (M=%d, K=%d), "
-                      "scaled linearly in N" % (CPU_SAMPLE_SWEEPS, cols, w["N"], w["M"], w["K"])}
+    out = {"value": sweeps_per_s, "unit": "sweeps/s", "cores": 1, "kind": "oracle",
+           "sample": "%d FP64 oracle sweeps (NumPy, 1 thread) on the first %d of %d columns (M=%d, K=%d), "
+                     "scaled linearly in N" % (CPU_SAMPLE_SWEEPS, cols, w["N"], w["M"], w["K"])}
+    ncpu = os.cpu_count() or 1
+    if ncpu > 1:
+        rm = cpu_sample(workload, cols, CPU_SAMPLE_SWEEPS, threads=ncpu)
+        out["all_cores"] = {"value": (1.0 / rm["sec_per_sweep"]) * cols / w["N"], "unit": "sweeps/s",
+                            "cores": ncpu, "sample": "same slice, %d BLAS threads" % ncpu}
+    return out
 
 
 # ------------------------------------------------------------------ main
