@@ -15,13 +15,14 @@
 //
 // Kernel structure (one CTA per SM, persistent over 64-column tiles):
 //   warp 0      producer: TMA bulk copies of the C-factor tile (once per
-//               column tile), the B-factor row block (from L2) and the X tile
-//               (64 column segments of 128 rows, double buffered);
+//               column tile) and the B-factor row block (from L2), and one
+//               2-D tensor copy of the 128 x 64 X tile (double buffered);
 //   warp 1      allocates 128 TMEM columns (two 128 x 64 float32 accumulators)
 //               and one elected thread issues the tcgen05.mma instructions;
-//   warps 4-7   epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
-//               lanes 32(w-4)..), R = X - D rounded to bfloat16, stored, and
-//               the sum of R^2 accumulated in float64.
+//   warps 4-11  epilogue, two warps per TMEM lane quarter (warp w reads lanes
+//               32 (w % 4).. and columns 32 ((w - 4) / 4)..): tcgen05.ld of the
+//               accumulator, R = X - D (rounded to bfloat16 for that mode),
+//               stored, and the sum of R^2 accumulated in float64.
 // Operands live in global memory pre-split and pre-tiled in the no-swizzle
 // K-major core-matrix layout (8 rows x 16 bytes per core matrix, core matrices
 // along K 128 bytes apart, along M/N Kp*E*8 bytes apart for E-byte elements),
@@ -34,13 +35,17 @@
 // TMEM and returns.
 #include "did_internal.cuh"
 
+#include <cudaTypedefs.h>
 #include <stdio.h>
+
+#include <mutex>
 
 namespace did {
 
 namespace {
 
-constexpr int kTcThreads = 256;     // 8 warps
+constexpr int kTcThreads = 384;     // 12 warps: producer, MMA, two idle, eight epilogue
+constexpr int kEpiWarps = 8;
 constexpr int kTileM = 128;         // rows per MMA (TMEM lanes)
 constexpr int kTileN = 64;          // columns per tile (MMA N)
 constexpr int kMaxKp = 128;         // K padded to a multiple of 16, at most 128 (bfloat16)
@@ -172,7 +177,7 @@ enum {
 
 // F32: TF32x3 operands and a float32 residual; otherwise BF16x3 and bfloat16.
 template <bool F32>
-__global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a) {
+__global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a, const __grid_constant__ CUtensorMap tmX) {
   constexpr int E = F32 ? 4 : 2;                  // operand element bytes
   constexpr int KSTEP = F32 ? 8 : 16;             // K per MMA (32 bytes)
   extern __shared__ __align__(1024) unsigned char sm[];
@@ -196,7 +201,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a) {
     *mma_steps = 0;
     for (int i = 0; i < BAR_COUNT; ++i) {
       const bool per_warp = (i == BAR_X_EMPTY || i == BAR_X_EMPTY + 1 || i == BAR_ACC_EMPTY || i == BAR_ACC_EMPTY + 1);
-      mbar_init(bars + i, per_warp ? 4 : 1);
+      mbar_init(bars + i, per_warp ? kEpiWarps : 1);
     }
   }
   fence_mbar_init();
@@ -233,17 +238,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a) {
         mbar_arrive_expect_tx(bars + BAR_A_FULL, a_bytes);
         bulk_load(sA, reinterpret_cast<const unsigned char*>(a.Ahl) + (size_t)rb * a_bytes, a_bytes,
                   bars + BAR_A_FULL);
-        // X tile: 64 column segments of up to 128 rows into buffer s & 1
+        // X tile: one 2-D tensor copy of rows rb*128.., columns j0.. into
+        // buffer s & 1 (element (row, c) at c*128 + row; rows past ld and
+        // columns past N are filled with zeros and count in the bytes)
         const int xb = (int)(s & 1);
         if (s >= 2 && !tc_wait(bars + BAR_X_EMPTY + xb, (uint32_t)(((s - 2) >> 1) & 1), err, tmo)) break;
-        const int i0 = rb * kTileM;
-        const int rows = a.ld - i0 < kTileM ? a.ld - i0 : kTileM;
-        const int ncol = a.N - j0 < kTileN ? (int)(a.N - j0) : kTileN;
-        mbar_arrive_expect_tx(bars + BAR_X_FULL + xb, (uint32_t)(rows * 4 * ncol));
-        float* xdst = sX + (size_t)xb * kTileN * kTileM;
-        for (int c = 0; c < ncol; ++c)
-          bulk_load(xdst + c * kTileM, a.X + (size_t)(j0 + c) * a.ld + i0, (uint32_t)(rows * 4),
-                    bars + BAR_X_FULL + xb);
+        mbar_arrive_expect_tx(bars + BAR_X_FULL + xb, (uint32_t)(kTileM * kTileN * 4));
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+            "[%4];" ::"r"(smem_u32(sX + (size_t)xb * kTileN * kTileM)),
+            "l"(reinterpret_cast<uint64_t>(&tmX)), "r"(rb * kTileM), "r"((int)j0), "r"(smem_u32(bars + BAR_X_FULL + xb))
+            : "memory");
       }
     }
   } else if (warp == 1) {
@@ -283,8 +288,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a) {
     }
   } else if (warp >= 4) {
     // ------------------------------------------------------------- epilogue
-    const int ew = warp - 4;                 // TMEM lane quarter
-    const int row_in = ew * 32 + lane;
+    const int ew = warp - 4;
+    const int quarter = warp & 3;            // TMEM lanes 32*quarter.. (the warp's own quarter)
+    const int c0 = (ew >> 2) * (kTileN / 2); // this warp's half of the tile's columns
+    const int row_in = quarter * 32 + lane;
     double acc2 = 0.0;
     bool ok = true;
     for (int64_t s = 0; s < nsteps && ok; ++s) {
@@ -296,22 +303,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a) {
       ok = tc_wait(bars + BAR_ACC_FULL + ab, (uint32_t)((s >> 1) & 1), err, tmo) &&
            tc_wait(bars + BAR_X_FULL + xb, (uint32_t)((s >> 1) & 1), err, tmo);
       tc_fence_after();
-      float d[kTileN];
+      float d[kTileN / 2];
 #pragma unroll
-      for (int c = 0; c < kTileN; c += 16)
-        tmem_ld16(tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(ab * kTileN + c), d + c);
+      for (int c = 0; c < kTileN / 2; c += 16)
+        tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ab * kTileN + c0 + c), d + c);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(bars + BAR_ACC_EMPTY + ab);
       const int i = rb * kTileM + row_in;
-      const float* xs = sX + (size_t)xb * kTileN * kTileM + row_in;
-      const int ncol = a.N - j0 < kTileN ? (int)(a.N - j0) : kTileN;
+      const float* xs = sX + (size_t)xb * kTileN * kTileM + (size_t)c0 * kTileM + row_in;
+      const int ncol = (a.N - j0 < kTileN ? (int)(a.N - j0) : kTileN) - c0;
       float s2 = 0.f;
       if (ok && i < a.ld) {
         if (F32) {
-          float* rp = static_cast<float*>(a.R) + (size_t)j0 * a.ld + i;
+          float* rp = static_cast<float*>(a.R) + (size_t)(j0 + c0) * a.ld + i;
 #pragma unroll
-          for (int c = 0; c < kTileN; ++c) {
+          for (int c = 0; c < kTileN / 2; ++c) {
             if (c < ncol) {
               const float r = xs[c * kTileM] - d[c];
               rp[(size_t)c * a.ld] = r;
@@ -319,9 +326,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a) {
             }
           }
         } else {
-          __nv_bfloat16* rp = static_cast<__nv_bfloat16*>(a.R) + (size_t)j0 * a.ld + i;
+          __nv_bfloat16* rp = static_cast<__nv_bfloat16*>(a.R) + (size_t)(j0 + c0) * a.ld + i;
 #pragma unroll
-          for (int c = 0; c < kTileN; ++c) {
+          for (int c = 0; c < kTileN / 2; ++c) {
             if (c < ncol) {
               const float r = xs[c * kTileM] - d[c];
               const __nv_bfloat16 rb16 = __float2bfloat16_rn(r);
@@ -336,7 +343,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a) {
       __syncwarp();
       if (lane == 0) mbar_arrive(bars + BAR_X_EMPTY + xb);
     }
-    // CTA partial of sum R^2 over the 4 epilogue warps, in warp order.
+    // CTA partial of sum R^2 over the epilogue warps, in warp order.
     acc2 = warp_sum_f64(acc2);
     if (lane == 0) red[ew] = acc2;
   }
@@ -353,7 +360,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a) {
   __syncthreads();
   tc_fence_after();
   if (warp == 1) tmem_dealloc(tmem, kTmemCols);
-  if (threadIdx.x == 0) a.part[blockIdx.x] = red[0] + red[1] + red[2] + red[3];
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kEpiWarps; ++w) t += red[w];
+    a.part[blockIdx.x] = t;
+  }
 }
 
 // ------------------------------------------------------------ operand prep
@@ -448,6 +459,20 @@ size_t refresh_tc_workspace_bytes(int M, int ld, int64_t N, int K, bool f32) {
 
 int refresh_tc_grid() { return sm_count_tc(); }
 
+// cuTensorMapEncodeTiled from the driver, through the runtime's entry-point query.
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
 template <typename T, bool F32>
 static cudaError_t launch_tc(const float* X, void* R, const float* B, const float* C, int M, int ld, int64_t N,
                              int K, void* workspace, double* part, int* err, uint64_t timeout_ns, cudaStream_t s) {
@@ -475,10 +500,23 @@ static cudaError_t launch_tc(const float* X, void* R, const float* B, const floa
   a.row_blocks = row_blocks;
   a.col_tiles = col_tiles;
   a.timeout_ns = timeout_ns;
+  // X as a 2-D float32 tensor: rows (ld, contiguous) x columns (N), row stride
+  // ld*4 bytes (ld is a multiple of 16, X 256-byte aligned), box 128 x 64.
+  PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+  if (!encode) return cudaErrorNotSupported;
+  CUtensorMap tmX;
+  const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)N};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)kTileM, (cuuint32_t)kTileN};
+  const cuuint32_t estr[2] = {1, 1};
+  if (encode(&tmX, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(X), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
   const size_t smem = tc_smem(Kp, (int)sizeof(T)).total;
   e = cudaFuncSetAttribute(refresh_tc_kernel<F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  refresh_tc_kernel<F32><<<sms, kTcThreads, smem, s>>>(a);
+  refresh_tc_kernel<F32><<<sms, kTcThreads, smem, s>>>(a, tmX);
   return cudaGetLastError();
 }
 
