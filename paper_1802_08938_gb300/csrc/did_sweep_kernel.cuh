@@ -600,7 +600,10 @@ __device__ __forceinline__ void column_pass(const SweepArgs& a, int cta, int k, 
       if (MODE != kPrologue) co1 = __ldcg(Ck + j + 2);
       cn1 = __ldcg(Cn + j + 2);
     }
-    pf_j = j + 1;
+    // co0/cn0 now hold column j+1 only if it lies in this unit; a group's next
+    // unit may start right at cu_hi (two consecutive units from the counter),
+    // and must then load its first column afresh.
+    pf_j = j + 1 < cu_hi ? j + 1 : -1;
     float cpo = 0.f, cpn = 0.f;             // pending c_{k-1,j} before and after its update
     if (LZ == 2) {
       cpo = __ldcg(a.Cold + j);
