@@ -344,6 +344,9 @@ def main():
                     help="requests of the serving stream to run (4096 in the full stream)")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrival rate, requests/s")
     ap.add_argument("--serve-only", action="store_true", help="run only the serving measurement")
+    ap.add_argument("--serve-sustain-rate", type=float, default=1.5,
+                    help="arrival rate (req/s) of the second, sustainable serving measurement (FP32); 0 = skip")
+    ap.add_argument("--serve-sustain-requests", type=int, default=24)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -545,6 +548,10 @@ def main():
     if not args.no_serve and not args.shape:
         serving = [serve_bench(did, args.serve_requests, args.serve_rate, did.DID_FP32),
                    serve_bench(did, args.serve_requests, args.serve_rate, did.DID_BF16R)]
+        if args.serve_sustain_rate > 0:
+            # below the measured capacity (~2.7 solves/s of 300-sweep requests):
+            # latencies are then service times plus a short queue
+            serving.append(serve_bench(did, args.serve_sustain_requests, args.serve_sustain_rate, did.DID_FP32))
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and not args.shape:
