@@ -79,6 +79,29 @@ def test_host_side_argument_checks_need_no_gpu(lib):
     assert not h.value
 
 
+@pytest.mark.parametrize("change", [
+    dict(flags=1 << 12),                                             # unknown flag bit
+    dict(flags=8 | 16),                                              # eager and lazy write-back together
+    dict(inner_c=2),                                                 # inner repeats outside the batched order
+    dict(order=2, inner_b=65),                                       # more than 64 repeats
+    dict(order=2, inner_c=-1),
+    dict(order=2, precision=1),                                      # batched order with a bfloat16 residual
+    dict(order=3),                                                   # no such order
+    dict(precision=2),                                               # no such precision
+    dict(stop=2),
+    dict(refresh_every=-1),
+])
+def test_invalid_options_rejected_before_any_cuda_call(lib, change):
+    import paper_1802_08938_gb300 as did
+    o = did.default_options()
+    for k, v in change.items():
+        setattr(o, k, v)
+    h = ctypes.c_void_p()
+    x = (ctypes.c_float * 64)()
+    assert did._lib.did_create_ex(x, 8, 8, 2, 0, ctypes.byref(o), ctypes.byref(h)) == did.DID_EINVAL
+    assert not h.value
+
+
 # ---------------------------------------------- struct layouts and constants
 STRUCTS = ["did_options", "did_info", "did_request", "did_result", "did_server_stats_t"]
 
