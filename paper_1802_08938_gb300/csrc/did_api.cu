@@ -423,7 +423,7 @@ const char* did_last_error(const did_ctx* ctx) { return ctx ? ctx->last_error.c_
 
 void did_destroy(did_ctx* ctx) {
   if (!ctx) return;
-  if (ctx->stream || true) cudaStreamSynchronize(ctx->stream);
+  cudaStreamSynchronize(ctx->stream);   // work queued on the context's stream may still use its buffers
   free_all(ctx);
   delete ctx;
 }
