@@ -224,7 +224,7 @@ did_status refresh_tc(did_ctx* c, double* f) {
 }
 
 did_status refresh(did_ctx* c) {
-  double s[3];
+  double s[3] = {0.0, 0.0, 0.0};
   did_status st;
   if (did::refresh_tc_supported(c->K, !c->bf16) && !(c->opt.flags & DID_FLAG_SIMT_REFRESH)) {
     double f = 0.0;
@@ -520,7 +520,7 @@ static did_status create_impl(did_ctx* c, const float* X, uint64_t seed) {
   if (st != DID_OK) return st;
 
   if (c->opt.init_scale) {
-    double s[3];
+    double s[3] = {0.0, 0.0, 0.0};
     st = dense(c, 2, s);
     if (st != DID_OK) return st;
     if (s[2] > 0.0 && s[1] > 0.0) {
@@ -598,7 +598,7 @@ did_status did_factor(did_ctx* c, int32_t max_iter, double tol, int32_t* iters_d
 
 did_status did_objective(did_ctx* c, double* obj) {
   if (!c || !obj) return DID_EINVAL;
-  double s[3];
+  double s[3] = {0.0, 0.0, 0.0};
   did_status st = dense(c, 1, s);
   if (st != DID_OK) return st;
   *obj = 0.5 * s[0];
