@@ -102,12 +102,15 @@ did_status plan_sweep(int ld, int64_t N, bool bf16, int grid_override, int64_t m
   // Column units.  SMs do not get equal shares of HBM bandwidth, so a fixed
   // split of the columns leaves the pass waiting for the slowest CTAs.  When
   // the partial rows fit in about 1% of the residual's traffic, groups take
-  // three tiers of units (60/30/10% of the columns) from a counter; otherwise
-  // each group takes one contiguous range and partials are summed per CTA.
+  // three tiers of units (60/30/10% of the columns; the last tier cut into
+  // kTier2Split units per group, so the tail of a pass is short) from a
+  // counter; otherwise each group takes one contiguous range and partials are
+  // summed per CTA.
   const int64_t TG = (int64_t)plan->grid * plan->NG;
-  const double part_frac = 3.0 * (double)TG * 4.0 / (2.0 * (double)N * elem);
+  const int64_t S2 = kTier2Split;          // last tier: S2 units per column group
+  const double part_frac = (double)(2 + S2) * (double)TG * 4.0 / (2.0 * (double)N * elem);
   bool dyn = N >= 8 * TG && part_frac <= 0.01;
-  if (max_units > 0 && 3 * TG + 2 > max_units) dyn = false;
+  if (max_units > 0 && (2 + S2) * TG + 2 > max_units) dyn = false;
   Units U{};
   if (dyn) {
     U.tg = TG;
@@ -115,7 +118,7 @@ did_status plan_sweep(int ld, int64_t N, bool bf16, int grid_override, int64_t m
     U.n0 = std::min<int64_t>(N, U.c0 * TG);
     U.c1 = std::max<int64_t>(1, (int64_t)(0.3 * (double)N / (double)TG));
     U.n1 = std::min<int64_t>(N, U.n0 + U.c1 * TG);
-    U.c2 = std::max<int64_t>(1, (N - U.n1 + TG - 1) / TG);
+    U.c2 = std::max<int64_t>(1, (N - U.n1 + S2 * TG - 1) / (S2 * TG));
     plan->nunits = (int)(2 * TG + (N - U.n1 + U.c2 - 1) / U.c2);
     plan->npart = plan->nunits;
   } else {

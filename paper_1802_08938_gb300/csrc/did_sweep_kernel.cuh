@@ -52,6 +52,10 @@ constexpr int kMaxStages = DID_MAX_STAGES;   // ring stages per column group (up
 #define DID_PAIRS 1
 #endif
 constexpr bool kPairs = DID_PAIRS != 0;      // c-passes may take columns in pairs
+#ifndef DID_TIER2_SPLIT
+#define DID_TIER2_SPLIT 2
+#endif
+constexpr int kTier2Split = DID_TIER2_SPLIT;   // units per column group in the last tier of dynamic units
 #ifndef DID_SERVE_PAIRS
 #define DID_SERVE_PAIRS 1
 #endif

@@ -60,7 +60,7 @@ def test_lazy_matches_oracle_and_eager(did, M, N, K):
 
 
 def test_lazy_dynamic_units_and_refresh(did):
-    M, N, K = 64, 400000, 4             # short columns, many of them: column units from a counter
+    M, N, K = 64, 500000, 4             # short columns, many of them: column units from a counter
     X, _, _ = W.planted(M, N, K, seed=77, sigma=0.05)
     B0, C0 = W.init_factors(M, N, K, 77)
     sweeps = 6
