@@ -109,7 +109,7 @@ did_status plan_sweep(int ld, int64_t N, bool bf16, int grid_override, int64_t m
   const int64_t TG = (int64_t)plan->grid * plan->NG;
   const int64_t S2 = kTier2Split;          // last tier: S2 units per column group
   const double part_frac = (double)(2 + S2) * (double)TG * 4.0 / (2.0 * (double)N * elem);
-  bool dyn = N >= 8 * TG && part_frac <= 0.01;
+  bool dyn = N >= 8 * TG && part_frac <= kDynMaxPartFrac;
   if (max_units > 0 && (2 + S2) * TG + 2 > max_units) dyn = false;
   Units U{};
   if (dyn) {

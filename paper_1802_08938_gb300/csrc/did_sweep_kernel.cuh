@@ -56,6 +56,10 @@ constexpr bool kPairs = DID_PAIRS != 0;      // c-passes may take columns in pai
 #define DID_TIER2_SPLIT 2
 #endif
 constexpr int kTier2Split = DID_TIER2_SPLIT;   // units per column group in the last tier of dynamic units
+#ifndef DID_DYN_MAX_PART_FRAC
+#define DID_DYN_MAX_PART_FRAC 0.01
+#endif
+constexpr double kDynMaxPartFrac = DID_DYN_MAX_PART_FRAC;   // partial-row traffic allowed for dynamic units
 #ifndef DID_SERVE_PAIRS
 #define DID_SERVE_PAIRS 1
 #endif

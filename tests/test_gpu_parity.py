@@ -276,3 +276,28 @@ def test_device_generator_matches_host_generator(did):
     Xd = torch.empty((N, M), device="cuda")
     did.did_generate_image(Xd, M, N, 7, 0.8)
     np.testing.assert_array_equal(Xd.cpu().numpy().T, W.image_like(M, N, 7))
+
+
+@pytest.mark.parametrize("order,flags", [("hals", "eager"), ("hals", "lazy"), ("dbcd", "eager")])
+def test_one_group_takes_consecutive_units(did, order, flags):
+    """One CTA with one 512-thread column group and dynamic units: the group
+    takes every unit in turn, so each new unit starts right after the previous
+    one -- the case where a stale prefetch of c once went unnoticed."""
+    M, N, K = 10000, 64, 3
+    X, _, _ = W.planted(M, N, K, seed=31, sigma=0.01)
+    B0, C0 = W.init_factors(M, N, K, 31)
+    ref = O.factor(X, B0, C0, order=order, max_iter=10, stop="none")
+    kw = dict(grid_ctas=1, order=did.DID_ORDER_INTERLEAVED if order == "hals" else did.DID_ORDER_DID,
+              flags=did.DID_FLAG_LAZY_WRITEBACK if flags == "lazy" else did.DID_FLAG_EAGER_WRITEBACK)
+    if order == "dbcd":
+        kw["flags"] = 0
+    got = run_gpu(did, X, B0, C0, 10, **kw)
+    info = got["info"]
+    print("one group, %s/%s: units %d dynamic %d GS %d grid %d" % (order, flags, info["column_units"],
+                                                                   info["dynamic_units"], info["group_threads"],
+                                                                   info["grid_ctas"]))
+    assert info["grid_ctas"] == 1 and info["group_threads"] == 512 and info["dynamic_units"] == 1
+    assert info["column_units"] >= 3
+    eB, eC = rel_fro(got["B"], ref["B"]), rel_fro(got["C"], ref["C"])
+    eF = rel_obj(got["trace"][-1], ref["trace"][-1], X)
+    assert eB <= TOL_FACTOR and eC <= TOL_FACTOR and eF <= TOL_OBJ
