@@ -283,7 +283,7 @@ def test_one_group_takes_consecutive_units(did, order, flags):
     """One CTA with one 512-thread column group and dynamic units: the group
     takes every unit in turn, so each new unit starts right after the previous
     one -- the case where a stale prefetch of c once went unnoticed."""
-    M, N, K = 10000, 64, 3
+    M, N, K = 10000, 400, 3
     X, _, _ = W.planted(M, N, K, seed=31, sigma=0.01)
     B0, C0 = W.init_factors(M, N, K, 31)
     ref = O.factor(X, B0, C0, order=order, max_iter=10, stop="none")
