@@ -164,18 +164,20 @@ def sweep_dbcd(X, B, C, R=None, on_block=None):
 
 
 def sweep_did(X, B, C, inner_c=1, inner_b=1):
-    """One iteration of DID (Algorithm 3), written as the paper states it.
+    """One iteration of DID (Algorithm 3): what it computes, in its order.
 
-    1. E := X - B C (every column recomputed from X).
-    2. C update by equations up:c.
-    3. W := E C^T (M x K; column i is sum_j e_j c_ij, matrix W_j summed over j)
-       and V := lower triangle of C C^T (V_j summed over j), one reduction.
-    4. For i = 1..K:
+    - The residual E := X - B C, every column recomputed from X.
+    - The C step: the updates of equations up:c.
+    - The one reduction: W := E C^T (M x K; column i is sum_j e_j c_ij, the
+      matrices W_j summed over j) and V := lower triangle of C C^T (the V_j
+      summed over j).
+    - The B step, for i = 1..K:
           b_i^{t+1} := [b_i^t + w_i / v_ii - sum_{k<i} (v_ik / v_ii) delta b_k]_+
           delta b_i := b_i^{t+1} - b_i^t
-    With inner repeats, step 2 runs inner_c times on the kept residual, and
-    steps 3-4 run inner_b times; before each further B repeat the residual
-    takes the paper's incremental rule E := E - delta b_i c_i for every i.
+    With inner repeats, the C step runs inner_c times on the kept residual,
+    and the reduction with the B step runs inner_b times; before each further
+    B repeat the residual takes the paper's incremental rule
+    E := E - delta b_i c_i for every i.
     inner_c = 0 (or inner_b = 0) leaves C (or B) fixed.
     Returns (B, C, degenerate_events).
     """
