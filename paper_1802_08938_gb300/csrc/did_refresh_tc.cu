@@ -15,8 +15,9 @@
 //
 // Kernel structure (one CTA per SM, persistent over 64-column tiles):
 //   warp 0      producer: TMA bulk copies of the C-factor tile (once per
-//               column tile) and the B-factor row block (from L2), and one
-//               2-D tensor copy of the 128 x 64 X tile (double buffered);
+//               column tile) and the B-factor row block (from L2; double
+//               buffered, so the next block loads while the MMAs run), and
+//               one 2-D tensor copy of the 128 x 64 X tile (double buffered);
 //   warp 1      allocates 128 TMEM columns (two 128 x 64 float32 accumulators)
 //               and one elected thread issues the tcgen05.mma instructions;
 //   warps 4-11  epilogue, two warps per TMEM lane quarter (warp w reads lanes
@@ -152,7 +153,7 @@ struct TcSmem {
 __host__ __device__ __forceinline__ TcSmem tc_smem(int Kp, int E) {
   TcSmem L;
   size_t o = 0;
-  L.A = o;    o += (size_t)2 * kTileM * Kp * E;          // Bh, Bl row block
+  L.A = o;    o += (size_t)2 * 2 * kTileM * Kp * E;      // two buffers of the Bh, Bl row block
   L.B = o;    o += (size_t)2 * kTileN * Kp * E;          // Ch, Cl column tile
   L.X = o;    o += (size_t)2 * kTileN * kTileM * 4;      // two X tiles [64 cols][128 rows]
   L.bars = o; o += 16 * sizeof(uint64_t);
@@ -166,13 +167,13 @@ __host__ __device__ __forceinline__ TcSmem tc_smem(int Kp, int E) {
 // Barrier slots.
 enum {
   BAR_B_FULL = 0,     // C-factor tile landed
-  BAR_A_FULL = 1,     // B-factor row block landed
-  BAR_A_EMPTY = 2,    // MMAs of the row block done reading A (and B)
-  BAR_X_FULL = 3,     // 3, 4: X tile buffers landed
-  BAR_X_EMPTY = 5,    // 5, 6: epilogue done with an X buffer (count 4 warps)
-  BAR_ACC_FULL = 7,   // 7, 8: accumulator ready (tcgen05.commit)
-  BAR_ACC_EMPTY = 9,  // 9, 10: epilogue done reading an accumulator (count 4 warps)
-  BAR_COUNT = 11
+  BAR_A_FULL = 1,     // 1, 2: B-factor row block buffers landed
+  BAR_A_EMPTY = 3,    // 3, 4: MMAs of a step done reading its A buffer (and B)
+  BAR_X_FULL = 5,     // 5, 6: X tile buffers landed
+  BAR_X_EMPTY = 7,    // 7, 8: epilogue done with an X buffer (one arrival per epilogue warp)
+  BAR_ACC_FULL = 9,   // 9, 10: accumulator ready (tcgen05.commit)
+  BAR_ACC_EMPTY = 11, // 11, 12: epilogue done reading an accumulator (one arrival per epilogue warp)
+  BAR_COUNT = 13
 };
 
 // F32: TF32x3 operands and a float32 residual; otherwise BF16x3 and bfloat16.
@@ -226,18 +227,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a, con
         const int rb = (int)(s % a.row_blocks);
         const int64_t tile = blockIdx.x + ti * gridDim.x;
         const int64_t j0 = tile * kTileN;
+        // A_EMPTY + (t & 1) completes once per use of buffer t & 1: for step t
+        // its phase parity is (t >> 1) & 1.
+        if (rb == 0 && s > 0) {
+          // the previous tile's MMAs (all of them: commits complete in order)
+          // must be done with the C-factor buffer
+          if (!tc_wait(bars + BAR_A_EMPTY + ((s - 1) & 1), (uint32_t)(((s - 1) >> 1) & 1), err, tmo)) break;
+        }
         if (rb == 0) {
-          // previous tile's MMAs must be done with the C-factor buffer
-          if (s > 0 && !tc_wait(bars + BAR_A_EMPTY, (uint32_t)((s - 1) & 1), err, tmo)) break;
           mbar_arrive_expect_tx(bars + BAR_B_FULL, b_bytes);
           bulk_load(sB, reinterpret_cast<const unsigned char*>(a.Bhl) + (size_t)tile * b_bytes, b_bytes,
                     bars + BAR_B_FULL);
-        } else {
-          if (!tc_wait(bars + BAR_A_EMPTY, (uint32_t)((s - 1) & 1), err, tmo)) break;
         }
-        mbar_arrive_expect_tx(bars + BAR_A_FULL, a_bytes);
-        bulk_load(sA, reinterpret_cast<const unsigned char*>(a.Ahl) + (size_t)rb * a_bytes, a_bytes,
-                  bars + BAR_A_FULL);
+        const int abuf = (int)(s & 1);
+        if (s >= 2 && !tc_wait(bars + BAR_A_EMPTY + abuf, (uint32_t)(((s - 2) >> 1) & 1), err, tmo)) break;
+        mbar_arrive_expect_tx(bars + BAR_A_FULL + abuf, a_bytes);
+        bulk_load(sA + (size_t)abuf * a_bytes, reinterpret_cast<const unsigned char*>(a.Ahl) + (size_t)rb * a_bytes,
+                  a_bytes, bars + BAR_A_FULL + abuf);
         // X tile: one 2-D tensor copy of rows rb*128.., columns j0.. into
         // buffer s & 1 (element (row, c) at c*128 + row; rows past ld and
         // columns past N are filled with zeros and count in the bytes)
@@ -261,8 +267,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a, con
         const int rb = (int)(s % a.row_blocks);
         const int64_t ti = s / a.row_blocks;
         if (rb == 0 && !tc_wait(bars + BAR_B_FULL, (uint32_t)(ti & 1), err, tmo)) break;
-        if (!tc_wait(bars + BAR_A_FULL, (uint32_t)(s & 1), err, tmo)) break;
-        const int ab = (int)(s & 1);
+        const int ab = (int)(s & 1);             // accumulator and A buffer of this step
+        if (!tc_wait(bars + BAR_A_FULL + ab, (uint32_t)((s >> 1) & 1), err, tmo)) break;
         if (s >= 2 && !tc_wait(bars + BAR_ACC_EMPTY + ab, (uint32_t)(((s - 2) >> 1) & 1), err, tmo)) break;
         tc_fence_after();
         const uint32_t d = tmem + (uint32_t)(ab * kTileN);
@@ -272,7 +278,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a, con
           const uint32_t aoff = prod == 2 ? a_split : 0u;
           const uint32_t boff = prod == 1 ? b_split : 0u;
           for (int kk = 0; kk < Kp / KSTEP; ++kk) {
-            const uint64_t ad = smem_desc(sA0 + aoff + (uint32_t)kk * 256u, 128u, sbo);
+            const uint64_t ad = smem_desc(sA0 + (uint32_t)ab * a_bytes + aoff + (uint32_t)kk * 256u, 128u, sbo);
             const uint64_t bd = smem_desc(sB0 + boff + (uint32_t)kk * 256u, 128u, sbo);
             if (F32)
               mma_tf32(d, ad, bd, idesc, acc);
@@ -282,7 +288,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a, con
           }
         }
         mma_commit(bars + BAR_ACC_FULL + ab);
-        mma_commit(bars + BAR_A_EMPTY);
+        mma_commit(bars + BAR_A_EMPTY + ab);
         *mma_steps = (int)(s + 1);
       }
     }
@@ -349,12 +355,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a, con
   }
 
   // Drain: every issued MMA must finish before TMEM is freed.  The last
-  // commit of the MMA thread arrives on BAR_A_EMPTY; its phase is waited here
+  // commit of the MMA thread arrives on BAR_A_EMPTY of its buffer; its phase is waited here
   // (bounded) by warp 1, then the allocation is released.
   __syncthreads();
   const int issued = *mma_steps;
   if (warp == 1 && lane == 0 && issued > 0) {
-    mbar_wait_bounded(bars + BAR_A_EMPTY, (uint32_t)((issued - 1) & 1), err, tmo);
+    mbar_wait_bounded(bars + BAR_A_EMPTY + ((issued - 1) & 1), (uint32_t)(((issued - 1) >> 1) & 1), err, tmo);
   }
   tc_fence_before();
   __syncthreads();
