@@ -287,6 +287,25 @@ def sweep_passes(K, lazy):
     return 2 * K - (K // 2 if lazy else 0)
 
 
+def max_over_ranks(x, ws):
+    """The largest value of x over the job's ranks (x itself with one rank).
+    The reduction tensor lives where the process group's backend wants it:
+    on the rank's GPU for NCCL, in host memory for gloo."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(ws, steps, max_ms):
+    """Whole-job throughput: units every rank processed over the slowest rank's time."""
+    return ws * steps / (max_ms / 1000.0)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -436,12 +455,8 @@ def main():
             phases = {"us_per_k": {"b_reduce+wait1": d(0, 1), "c_pass": d(1, 2), "wait2": d(2, 3),
                                    "gap_to_next_k": float((t[1:, 0] - t[:-1, 3]).mean() / 1e3) if len(t) > 1 else 0.0},
                       "k_steps": int(len(t))}
-    ms = ev0.elapsed_time(ev1)
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * args.steps / (ms / 1000.0)
+    ms = max_over_ranks(ev0.elapsed_time(ev1), ws)
+    value = job_value(ws, args.steps, ms)
 
     # Roofline of the sweep kernel: algorithmic bytes / its own event time.
     launches = info1["sweep_launches"] - info0["sweep_launches"]
@@ -533,11 +548,7 @@ def main():
         did.did_get_factors(c2.h, Bh, Ch)
         t1 = time.perf_counter()
         c2.close()
-        e_sec = t1 - t0
-        if ws > 1:
-            t = torch.tensor([e_sec], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e_sec = float(t.item())
+        e_sec = max_over_ranks(t1 - t0, ws)
         e2e = {"value": ws * args.steps / e_sec, "unit": "sweeps/s",
                "h2d_bytes_per_step": int(M * N * 4 / args.steps),
                "d2h_bytes_per_step": int((M * K + K * N) * 4 / args.steps),

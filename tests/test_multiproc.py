@@ -1,0 +1,69 @@
+"""The N > 1 path of the benchmark on CPU ranks (gloo, world size 2).
+
+Every GPU runs an independent replica (the sweep does not shard: one GPU per
+factorisation), so the only cross-rank steps are the barrier and the
+max-over-ranks timing that makes the whole-job value.  They are checked with
+two gloo ranks; the reference arm is launched the way the benchmark is for
+N > 1 (torch.distributed.run, one process per rank) and must print one line,
+from rank 0 only.
+"""
+
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, ws, port, out):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    sys.path.insert(0, ROOT)
+    import bench
+    ms = bench.max_over_ranks(100.0 + 50.0 * rank, ws)   # rank 1 is the slower one
+    dist.barrier()
+    out.put((rank, ms, bench.job_value(ws, 10, ms)))
+    dist.destroy_process_group()
+
+
+def test_max_over_ranks_and_job_value_with_gloo():
+    torch = pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, ms, value in res:
+        assert ms == 150.0                       # the slowest rank's time on every rank
+        assert abs(value - 2 * 10 / 0.150) < 1e-9  # units of both ranks over that time
+
+
+def test_reference_arm_under_torchrun_prints_once():
+    pytest.importorskip("torch")
+    port = free_port()
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), "bench.py", "--impl", "reference",
+           "--workload", "planted_uniform_200x1000_k10", "--gpus", "2", "--steps", "1", "--warmup", "3"]
+    r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
