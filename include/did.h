@@ -110,7 +110,10 @@ typedef struct {
 /* did_options.flags (DID_ORDER_DID_BATCHED only): run the sweep's float32
  * GEMMs through cuBLAS's float32 emulation on the bfloat16 tensor cores (each
  * operand split into three bfloat16 terms, all nine products accumulated in
- * float32) instead of pedantic float32 SIMT arithmetic. */
+ * float32) instead of pedantic float32 SIMT arithmetic.  The emulation has a
+ * large fixed cost per GEMM: it is faster only when M and K are large (on one
+ * GB300, 1.5x at 5000 x 200000 with K = 50, 7x slower at 784 x 70000 with
+ * K = 16). */
 #define DID_FLAG_GEMM_BF16X9 4
 /* did_options.flags (DID_ORDER_INTERLEAVED): deferred write-back defers the
  * write of R for k to the pass for k+1 (one write per pair of k, three passes
