@@ -68,6 +68,7 @@ struct did_ctx {
   int64_t refreshes = 0;
   int64_t last_refresh_at = -1;
   bool need_prologue = true;
+  int npart_first = 0;   // > 0: the partials for c_1 are the refresh's rows (no prologue)
   bool need_refresh = false;
   double last_obj = 0.0;
   size_t device_bytes = 0;
@@ -200,11 +201,18 @@ did_status refresh_tc(did_ctx* c, double* f) {
   }
   std::vector<double> part(G);
   int herr = 0;
+  // The interleaved order's first b-update takes the partials of R c_1^T
+  // that the refresh forms in its epilogue (the P and CCp buffers hold at
+  // least 2 G rows); the other orders do not use them.
+  const bool fuse = c->opt.order == DID_ORDER_INTERLEAVED;
+  c->need_prologue = true;
+  c->npart_first = 0;
   DID_CUDA(c, cudaMemsetAsync(c->tc_err, 0, sizeof(int), c->stream));
   DID_CUDA(c, cudaEventRecord(c->ev0, c->stream));
   DID_CUDA(c, did::launch_refresh_tc(c->X, c->R, c->B, c->C, (int)c->M, c->ld, c->N, c->K, c->tc_ws, c->tc_part,
-                                     c->tc_err, c->opt.timeout_ns ? c->opt.timeout_ns : kDefaultTimeoutNs,
-                                     c->stream, !c->bf16));
+                                     fuse ? c->P : nullptr, fuse ? c->CCp : nullptr, c->tc_err,
+                                     c->opt.timeout_ns ? c->opt.timeout_ns : kDefaultTimeoutNs, c->stream,
+                                     !c->bf16));
   DID_CUDA(c, cudaEventRecord(c->ev1, c->stream));
   DID_CUDA(c, cudaMemcpyAsync(part.data(), c->tc_part, sizeof(double) * G, cudaMemcpyDeviceToHost, c->stream));
   DID_CUDA(c, cudaMemcpyAsync(&herr, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -220,6 +228,7 @@ did_status refresh_tc(did_ctx* c, double* f) {
   double sum = 0.0;
   for (int i = 0; i < G; ++i) sum += part[i];
   *f = 0.5 * sum;
+  if (fuse) c->npart_first = 2 * G;
   return DID_OK;
 }
 
@@ -234,10 +243,11 @@ did_status refresh(did_ctx* c) {
   } else {
     st = dense(c, 0, s);
     if (st != DID_OK) return st;
+    c->npart_first = 0;
   }
   c->last_obj = 0.5 * s[0];
   if (c->batched) DID_CUDA(c, did::batched_reset(c->batched, c->Y, c->ld, c->K, s[0], c->stream));
-  c->need_prologue = true;
+  c->need_prologue = c->npart_first == 0;
   c->need_refresh = false;
   c->last_refresh_at = c->sweeps_done;
   c->refreshes++;
@@ -277,6 +287,7 @@ did_status launch_sweeps(did_ctx* c, int n, int stop_rule, double tol, int* done
   a.npart = c->plan.npart;
   a.n_sweeps = n;
   a.prologue = c->need_prologue ? 1 : 0;
+  a.npart_first = a.prologue ? 0 : c->npart_first;
   a.f_prev = c->trace.back();
   a.f0 = c->trace.front();
   a.stop_rule = stop_rule;
@@ -312,6 +323,7 @@ did_status launch_sweeps(did_ctx* c, int n, int stop_rule, double tol, int* done
                 "state kept, residual will be recomputed", h.err);
   }
   c->need_prologue = false;
+  if (n > 0) c->npart_first = 0;   // the launch's last pass formed the next partials
   for (int s = 0; s < h.sweeps; ++s) c->trace.push_back(c->trace_host[s]);
   c->sweeps_done += h.sweeps;
   if (h.sweeps > 0) c->last_obj = c->trace.back();
@@ -461,7 +473,8 @@ static did_status create_impl(did_ctx* c, const float* X, uint64_t seed) {
   c->B = c->Y + (size_t)K * c->ld;
   DID_CUDA(c, cudaMemsetAsync(c->Y, 0, (size_t)c->ld * K * sizeof(float), c->stream));
   ALLOC(C, (size_t)K * N * sizeof(float));
-  const size_t U = (size_t)std::max(c->plan.npart, G);
+  // partial rows: the plan's, and the tensor-core refresh's two per CTA
+  const size_t U = (size_t)std::max(std::max(c->plan.npart, G), 2 * did::refresh_tc_grid());
   ALLOC(P, U * c->ld * sizeof(float));
   ALLOC(CCp, U * sizeof(double));
   ALLOC(Sp, (size_t)2 * G * sizeof(double));

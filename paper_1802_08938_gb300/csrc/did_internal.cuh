@@ -293,6 +293,8 @@ struct SweepArgs {
   int dynamic;        // 1: groups take units from a counter, partials per unit;
                       // 0: group g takes unit g, partials per CTA
   int npart;          // partial rows the b-reduce adds (nunits or grid)
+  int npart_first;    // > 0: the first b-reduce of the launch adds this many
+                      // rows instead (partials written by the dense refresh)
   int n_sweeps;       // sweeps of this launch
   int prologue;       // 1: first form the partials of R c_1^T from R
   double f_prev;      // objective before the first sweep of this launch
@@ -355,13 +357,16 @@ int dense_grid();
 cudaError_t launch_dense(const DenseArgs& a, cudaStream_t s);
 
 // Tensor-core refresh R = X - B C: BF16x3 products for a bfloat16 residual
-// (K <= 128), TF32x3 for a float32 one (f32, K <= 64).
+// (K <= 128), TF32x3 for a float32 one (f32, K <= 64).  With P1 non-null it
+// also writes the partials of R c_1^T (2 refresh_tc_grid() rows of ld floats,
+// row 2 cta + column half) and of ||c_1||^2 (CC1, as many doubles), in the
+// layout the sweep's first b-reduce takes through SweepArgs::npart_first.
 bool refresh_tc_supported(int K, bool f32);
 size_t refresh_tc_workspace_bytes(int M, int ld, int64_t N, int K, bool f32);
 int refresh_tc_grid();
 cudaError_t launch_refresh_tc(const float* X, void* R, const float* B, const float* C, int M, int ld, int64_t N,
-                              int K, void* workspace, double* part, int* err, uint64_t timeout_ns, cudaStream_t s,
-                              bool f32);
+                              int K, void* workspace, double* part, float* P1, double* CC1, int* err,
+                              uint64_t timeout_ns, cudaStream_t s, bool f32);
 
 // Batched DID (Algorithm 3 with one reduction per sweep; cuBLAS GEMMs).
 struct BatchedState;

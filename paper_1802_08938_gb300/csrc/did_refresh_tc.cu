@@ -23,7 +23,12 @@
 //   warps 4-11  epilogue, two warps per TMEM lane quarter (warp w reads lanes
 //               32 (w % 4).. and columns 32 ((w - 4) / 4)..): tcgen05.ld of the
 //               accumulator, R = X - D (rounded to bfloat16 for that mode),
-//               stored, and the sum of R^2 accumulated in float64.
+//               stored, and the sum of R^2 accumulated in float64.  When
+//               asked, the epilogue also forms the partials of R c_1^T that
+//               the first b-update of the next sweep needs (one row of
+//               partials per CTA and column half, summed over the CTA's
+//               tiles in order) and ||c_1||^2 per CTA and half, so the sweep
+//               needs no extra read of R after a refresh.
 // Operands live in global memory pre-split and pre-tiled in the no-swizzle
 // K-major core-matrix layout (8 rows x 16 bytes per core matrix, core matrices
 // along K 128 bytes apart, along M/N Kp*E*8 bytes apart for E-byte elements),
@@ -59,6 +64,9 @@ struct TcArgs {
   const void* Ahl;           // [row blocks][2][128 rows x Kp] tiled B factor (hi, lo)
   const void* Bhl;           // [col tiles][2][64 cols x Kp] tiled C factor (hi, lo)
   double* part;              // [grid] sum of R^2 per CTA
+  const float* c1;           // row 1 of C (N floats), or null: no partials
+  float* P1;                 // [2 grid][ld] partials of R c_1^T (row 2 cta + column half)
+  double* CC1;               // [2 grid] partials of ||c_1||^2
   int* err;                  // error word
   int M, ld, Kp;
   int64_t N;
@@ -298,7 +306,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a, con
     const int quarter = warp & 3;            // TMEM lanes 32*quarter.. (the warp's own quarter)
     const int c0 = (ew >> 2) * (kTileN / 2); // this warp's half of the tile's columns
     const int row_in = quarter * 32 + lane;
-    double acc2 = 0.0;
+    const int half = ew >> 2;
+    float* prow = a.c1 ? a.P1 + (size_t)(2 * blockIdx.x + half) * a.ld : nullptr;
+    double acc2 = 0.0, cc1 = 0.0;
     bool ok = true;
     for (int64_t s = 0; s < nsteps && ok; ++s) {
       const int64_t ti = s / a.row_blocks;
@@ -306,8 +316,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a, con
       const int64_t tile = blockIdx.x + ti * gridDim.x;
       const int64_t j0 = tile * kTileN;
       const int ab = (int)(s & 1), xb = (int)(s & 1);
+      const int i = rb * kTileM + row_in;
+      const int ncol = (a.N - j0 < kTileN ? (int)(a.N - j0) : kTileN) - c0;
+      // Loads for the partials go out before the waits: this row's running
+      // sum (written by this thread one tile earlier) and c_1 on this half of
+      // the tile, one column per lane.
+      float pold = 0.f, cv = 0.f;
+      if (prow) {
+        if (ti > 0 && i < a.ld) pold = __ldcg(prow + i);
+        if (lane < ncol) cv = __ldg(a.c1 + j0 + c0 + lane);
+      }
       ok = tc_wait(bars + BAR_ACC_FULL + ab, (uint32_t)((s >> 1) & 1), err, tmo) &&
            tc_wait(bars + BAR_X_FULL + xb, (uint32_t)((s >> 1) & 1), err, tmo);
+      // the warp-wide tcgen05.ld below needs every lane, so the lanes agree
+      ok = __all_sync(0xffffffffu, ok);
       tc_fence_after();
       float d[kTileN / 2];
 #pragma unroll
@@ -316,9 +338,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a, con
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(bars + BAR_ACC_EMPTY + ab);
-      const int i = rb * kTileM + row_in;
       const float* xs = sX + (size_t)xb * kTileN * kTileM + (size_t)c0 * kTileM + row_in;
-      const int ncol = (a.N - j0 < kTileN ? (int)(a.N - j0) : kTileN) - c0;
       float s2 = 0.f;
       if (ok && i < a.ld) {
         if (F32) {
@@ -329,6 +349,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a, con
               const float r = xs[c * kTileM] - d[c];
               rp[(size_t)c * a.ld] = r;
               s2 = fmaf(r, r, s2);
+              d[c] = r;
             }
           }
         } else {
@@ -341,13 +362,33 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a, con
               rp[(size_t)c * a.ld] = rb16;
               const float rr = __bfloat162float(rb16);
               s2 = fmaf(rr, rr, s2);
+              d[c] = rr;
             }
           }
         }
       }
+      if (prow) {
+        // Partial of row i over this CTA's tiles, in tile order, from the
+        // stored (rounded) R as the sweep would read it; c_1 comes from the
+        // lane that loaded it (zero past N).
+        float p1 = 0.f;
+#pragma unroll
+        for (int c = 0; c < kTileN / 2; ++c) p1 = fmaf(d[c], __shfl_sync(0xffffffffu, cv, c), p1);
+        if (ok && i < a.ld) __stcg(prow + i, pold + p1);
+        // ||c_1||^2 over this half of the tile, once per tile (row block 0)
+        if (quarter == 0 && rb == 0) cc1 += (double)cv * (double)cv;
+      }
       acc2 += (double)s2;
       __syncwarp();
       if (lane == 0) mbar_arrive(bars + BAR_X_EMPTY + xb);
+    }
+    // A CTA without tiles still owns its partial rows: they are zero.
+    if (prow && ntile_cta == 0)
+      for (int rb = 0; rb < a.row_blocks; ++rb)
+        if (rb * kTileM + row_in < a.ld) __stcg(prow + rb * kTileM + row_in, 0.f);
+    if (a.c1 && quarter == 0) {
+      cc1 = warp_sum_f64(cc1);
+      if (lane == 0) a.CC1[2 * blockIdx.x + half] = cc1;
     }
     // CTA partial of sum R^2 over the epilogue warps, in warp order.
     acc2 = warp_sum_f64(acc2);
@@ -481,7 +522,8 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 
 template <typename T, bool F32>
 static cudaError_t launch_tc(const float* X, void* R, const float* B, const float* C, int M, int ld, int64_t N,
-                             int K, void* workspace, double* part, int* err, uint64_t timeout_ns, cudaStream_t s) {
+                             int K, void* workspace, double* part, float* P1, double* CC1, int* err,
+                             uint64_t timeout_ns, cudaStream_t s) {
   const int Kp = (K + 15) / 16 * 16;
   const int row_blocks = (ld + kTileM - 1) / kTileM;
   const int64_t col_tiles = (N + kTileN - 1) / kTileN;
@@ -498,6 +540,9 @@ static cudaError_t launch_tc(const float* X, void* R, const float* B, const floa
   a.Ahl = Ahl;
   a.Bhl = Bhl;
   a.part = part;
+  a.c1 = P1 ? C : nullptr;   // row 1 of the row-major K x N factor
+  a.P1 = P1;
+  a.CC1 = CC1;
   a.err = err;
   a.M = M;
   a.ld = ld;
@@ -527,11 +572,12 @@ static cudaError_t launch_tc(const float* X, void* R, const float* B, const floa
 }
 
 cudaError_t launch_refresh_tc(const float* X, void* R, const float* B, const float* C, int M, int ld, int64_t N, int K,
-                              void* workspace, double* part, int* err, uint64_t timeout_ns, cudaStream_t s,
-                              bool f32) {
+                              void* workspace, double* part, float* P1, double* CC1, int* err, uint64_t timeout_ns,
+                              cudaStream_t s, bool f32) {
   if (!refresh_tc_supported(K, f32)) return cudaErrorInvalidValue;
-  return f32 ? launch_tc<float, true>(X, R, B, C, M, ld, N, K, workspace, part, err, timeout_ns, s)
-             : launch_tc<__nv_bfloat16, false>(X, R, B, C, M, ld, N, K, workspace, part, err, timeout_ns, s);
+  return f32 ? launch_tc<float, true>(X, R, B, C, M, ld, N, K, workspace, part, P1, CC1, err, timeout_ns, s)
+             : launch_tc<__nv_bfloat16, false>(X, R, B, C, M, ld, N, K, workspace, part, P1, CC1, err, timeout_ns,
+                                               s);
 }
 
 }  // namespace did

@@ -808,7 +808,9 @@ __device__ __forceinline__ void column_pass(const SweepArgs& a, int cta, int k, 
 
 // b-reduce for block k: s = sum over the partial rows of P (fixed order), b_k'
 // from the closed form, ||b_k'||^2 and b_k'.b_k partials of this CTA's row
-// slice.  Each round covers `rows` rows of the slice with S = min(16, npart)
+// slice.  U partial rows (a.npart unless given: the first b-reduce after a
+// tensor-core refresh adds the refresh's rows).  Each round covers `rows`
+// rows of the slice with S = min(16, U)
 // interleaved subsets of the partial rows per row (thread t: row t % rows,
 // subset t / rows, up to 16 loads in flight); the subsets' sums are added in
 // subset order, then one thread per row forms b_k'.  With few partial rows
@@ -818,9 +820,9 @@ __device__ __forceinline__ void column_pass(const SweepArgs& a, int cta, int k, 
 // b_{k-1} from a.bold (read before this reduce overwrites it) and the two dot
 // products summed over a.XCp in float64.
 __device__ __forceinline__ void b_reduce(const SweepArgs& a, int cta, int G, int k, float* acc, double* bc,
-                                         double* dscr, bool corr = false) {
+                                         double* dscr, bool corr = false, int U = 0) {
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  const int U = a.npart;
+  if (U <= 0) U = a.npart;
   if (w == 0) {
     const double cc = warp_sum_global_f64(a.CCp, U, 1);
     if (l == 0) bc[0] = cc;
@@ -1040,8 +1042,9 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a, int cta, int ncta
       const int step = s * a.K + k;
       const bool rec = stamps && step < a.tstamp_cap;
       if (rec) a.tstamp[4 * step + 0] = globaltimer_ns();
-      // after a deferred pass (k odd) the partials lack the pending change
-      b_reduce(a, cta, G, k, sm.red, bc, sm.dscr, lazy && (k & 1));
+      // after a deferred pass (k odd) the partials lack the pending change;
+      // right after a tensor-core refresh the first partials are its rows
+      b_reduce(a, cta, G, k, sm.red, bc, sm.dscr, lazy && (k & 1), s == 0 && k == 0 ? a.npart_first : 0);
       DID_GRID_SYNC();
       if (rec) a.tstamp[4 * step + 1] = globaltimer_ns();
       if (w == 0) {

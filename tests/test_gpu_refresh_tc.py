@@ -131,3 +131,40 @@ def test_tensor_core_refresh_in_an_fp32_run(did):
     print("FP32 20 sweeps, TF32x3 refresh every 2: tc refreshes %d, relB %.3g, max relf %.3g" % (n_tc, eB, eF))
     assert n_tc == 10
     assert eB <= 1e-4 and eF <= 1e-5
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16r"])
+@pytest.mark.parametrize("M,N,K", [(300, 50, 4), (517, 777, 16), (1000, 20000, 20), (130, 3, 3)])
+def test_refresh_forms_first_partials(did, M, N, K, precision):
+    """The tensor-core refresh also forms the partials of R c_1^T for the next
+    sweep's first b-update (no prologue pass over R).  A run with a refresh
+    before sweeps 1, 3 and 5 matches the oracle's interleaved sweeps and the
+    SIMT-refresh run, which re-forms those partials in a prologue pass.  N = 50
+    and N = 3 leave most CTAs of the refresh without a column tile."""
+    from oracle import did_oracle as O
+    X, _, _ = W.planted(M, N, K, seed=3 * M + N, sigma=0.01)
+    B0, C0 = W.init_factors(M, N, K, 5)
+    Xc = np.ascontiguousarray(X.T)
+    prec = did.DID_FP32 if precision == "fp32" else did.DID_BF16R
+    kw = dict(B_init=np.ascontiguousarray(B0.T), C_init=C0, precision=prec, refresh_every=2)
+    with did.Context(Xc, M, N, K, **kw) as tc, did.Context(Xc, M, N, K, flags=did.DID_FLAG_SIMT_REFRESH, **kw) as simt:
+        tc.sweep(5)
+        simt.sweep(5)
+        i_tc, i_simt = tc.info(), simt.info()
+        B, C = tc.factors()
+        Bs, Cs = simt.factors()
+    assert i_tc["tc_refreshes"] == 3 and i_tc["prologue_launches"] == 0
+    assert i_simt["tc_refreshes"] == 0 and i_simt["prologue_launches"] == 3
+    ref = O.factor(X, B0, C0, order="hals", max_iter=5, stop="none")
+
+    def rel(a, b):
+        return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
+    eB, eC = rel(B, ref["B"]), rel(C, ref["C"])
+    dB, dC = rel(B, Bs.astype(np.float64)), rel(C, Cs.astype(np.float64))
+    print("%s M=%d N=%d K=%d: vs oracle B %.3g C %.3g, vs SIMT-refresh run B %.3g C %.3g"
+          % (precision, M, N, K, eB, eC, dB, dC))
+    # float32: within the parity bound; a bfloat16 residual rounds each stored
+    # entry by half an ulp (2^-9), which the oracle does not
+    tol = 1e-4 if precision == "fp32" else 4e-3
+    assert eB <= tol and eC <= tol
+    assert dB <= tol and dC <= tol
