@@ -234,7 +234,9 @@ did_status did_refresh_residual(did_ctx* ctx);
 did_status did_get_factors(did_ctx* ctx, float* B, float* C);
 
 /* Replace B and C (host or device sources, same layouts; must be finite and
- * >= 0) and recompute R.  With did_get_factors this is checkpoint/resume. */
+ * >= 0) and recompute R.  With did_get_factors this is checkpoint/resume.
+ * Both sources are checked before anything is copied: on DID_EINVAL the
+ * context keeps its factors and residual. */
 did_status did_set_factors(did_ctx* ctx, const float* B, const float* C);
 
 /* Copy the stored residual out as float32 M x N column-major (host or device). */

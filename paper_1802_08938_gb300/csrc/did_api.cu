@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -149,6 +150,25 @@ did_status check_nonneg(did_ctx* c, const float* p, int rows, int ld, int64_t co
   unsigned long long nbad = 0;
   DID_CUDA(c, cudaMemcpyAsync(&nbad, c->bad, sizeof(nbad), cudaMemcpyDeviceToHost, c->stream));
   DID_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (nbad) return fail(c, DID_EINVAL, "%s has %llu negative or non-finite entries", what, nbad);
+  return DID_OK;
+}
+
+// The same check on a caller's buffer of rows x cols floats (dense), before
+// anything is copied from it: on the device for device or managed memory,
+// here for host memory.
+did_status check_source(did_ctx* c, const float* p, int64_t rows, int64_t cols, const char* what) {
+  cudaPointerAttributes attr{};
+  const cudaError_t e = cudaPointerGetAttributes(&attr, p);
+  cudaGetLastError();
+  if (e == cudaSuccess && (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged))
+    return check_nonneg(c, p, (int)rows, (int)rows, cols, what);
+  unsigned long long nbad = 0;
+  const size_t n = (size_t)rows * (size_t)cols;
+  for (size_t i = 0; i < n; ++i) {
+    const float v = p[i];
+    if (!(v >= 0.f) || !std::isfinite(v)) ++nbad;
+  }
   if (nbad) return fail(c, DID_EINVAL, "%s has %llu negative or non-finite entries", what, nbad);
   return DID_OK;
 }
@@ -642,13 +662,15 @@ did_status did_get_factors(did_ctx* c, float* B, float* C) {
 
 did_status did_set_factors(did_ctx* c, const float* B, const float* C) {
   if (!c || !B || !C) return DID_EINVAL;
-  did_status st = copy_in_padded(c, c->B, c->ld, B, c->M, c->K);
+  // Both sources are checked before either is copied: a rejected call leaves
+  // the factors and the residual as they were.
+  did_status st = check_source(c, B, c->M, c->K, "B");
+  if (st != DID_OK) return st;
+  st = check_source(c, C, c->K, c->N, "C");
+  if (st != DID_OK) return st;
+  st = copy_in_padded(c, c->B, c->ld, B, c->M, c->K);
   if (st != DID_OK) return st;
   DID_CUDA(c, cudaMemcpyAsync(c->C, C, (size_t)c->K * c->N * sizeof(float), cudaMemcpyDefault, c->stream));
-  st = check_nonneg(c, c->B, (int)c->M, c->ld, c->K, "B");
-  if (st != DID_OK) return st;
-  st = check_nonneg(c, c->C, c->K, c->K, c->N, "C");
-  if (st != DID_OK) return st;
   return refresh(c);
 }
 

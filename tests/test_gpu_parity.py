@@ -159,6 +159,49 @@ def test_refresh_and_resume(did):
     assert np.max(np.abs(full["R"] - R_def)) < 1e-4 * max(1.0, np.abs(X).max())
 
 
+def test_rejected_set_factors_leaves_context_unchanged(did):
+    """Factors with a negative or non-finite entry are refused (DID_EINVAL)
+    before anything is copied, from host or device memory: the run then
+    continues bit for bit as if the call had not been made."""
+    import torch
+    X, M, N, K = W.make("planted_uniform_200x1000_k10", seed=8, M=150, N=700, K=6)
+    B0, C0 = W.init_factors(M, N, K, 8)
+    Xc = np.ascontiguousarray(X.T)
+    kw = dict(B_init=np.ascontiguousarray(B0.T), C_init=C0, refresh_every=3)
+    with did.Context(Xc, M, N, K, **kw) as a, did.Context(Xc, M, N, K, **kw) as b:
+        a.sweep(2)
+        b.sweep(2)
+        B, C = a.factors()
+        bad = []
+        Bn = B.copy()
+        Bn[7, 2] = -1e-3
+        bad.append((Bn, C))
+        Cn = C.copy()
+        Cn[1, 11] = np.nan
+        bad.append((B, Cn))
+        Ci = C.copy()
+        Ci[5, 0] = np.inf
+        bad.append((B, Ci))
+        for Bx, Cx in bad:
+            with pytest.raises(did.DIDError) as e:
+                a.set_factors(Bx, Cx)
+            assert e.value.status == did.DID_EINVAL
+        # device sources: B transposed to the library's column-major layout
+        Bd = torch.as_tensor(np.ascontiguousarray(Bn.T), device="cuda")
+        Cd = torch.as_tensor(np.ascontiguousarray(C), device="cuda")
+        with pytest.raises(did.DIDError) as e:
+            did.did_set_factors(a.h, Bd, Cd)
+        assert e.value.status == did.DID_EINVAL
+        a.sweep(4)
+        b.sweep(4)
+        Ba, Ca = a.factors()
+        Bb, Cb = b.factors()
+        ta, tb = a.trace(), b.trace()
+    np.testing.assert_array_equal(Ba, Bb)
+    np.testing.assert_array_equal(Ca, Cb)
+    np.testing.assert_array_equal(ta, tb)
+
+
 def test_factor_stopping_rule(did):
     X, M, N, K = W.make("planted_uniform_200x1000_k10", seed=6, M=100, N=400, K=5)
     B0, C0 = W.init_factors(M, N, K, 6)
