@@ -304,8 +304,12 @@ did_status did_generate_uniform(float* out_dev, int64_t n, uint64_t seed, int32_
 typedef struct did_server did_server;
 
 typedef struct {
-    const float* X;      /* host or device, M x N column-major; NULL: generate
-                            X = B0 C0 + 0.01 |N(0,1)| with B0, C0 ~ U[0,1) from seed */
+    const float* X;      /* host or device, M x N column-major, finite and >= 0
+                            (else the request fails with DID_EINVAL); read when
+                            the request is admitted, so the caller keeps it valid
+                            and unchanged until the request has finished.  NULL:
+                            generate X = B0 C0 + 0.01 |N(0,1)| with B0, C0 ~
+                            U[0,1) from seed */
     int64_t M, N;
     int32_t K;
     uint64_t seed;
@@ -338,8 +342,11 @@ typedef struct {
  * the server creates its own. */
 did_status did_server_create(size_t hbm_budget_bytes, did_precision precision, int32_t max_slots,
                              int32_t round_sweeps, void* stream, did_server** out);
-/* Queue a request (copied); *ticket identifies it.  DID_E_TOO_LARGE if it can
- * never fit (M beyond the kernel's limit or its memory above the budget). */
+/* Queue a request (the struct is copied; X is read at admission); *ticket
+ * identifies it.  DID_E_TOO_LARGE if it can never fit (M beyond the kernel's
+ * limit or its memory above the budget).  A request that fails (invalid X,
+ * out of memory, a device wait that ran out) fails alone: the server goes on
+ * with the others. */
 did_status did_server_submit(did_server* srv, const did_request* req, uint64_t* ticket);
 /* DID_PENDING while queued or running, else the request's final status. */
 did_status did_server_poll(did_server* srv, uint64_t ticket, did_result* res);

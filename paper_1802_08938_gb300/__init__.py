@@ -415,17 +415,25 @@ class Server:
     def __init__(self, hbm_budget_bytes, precision=DID_FP32, max_slots=64, round_sweeps=4, stream=None):
         self.h = did_server_create(hbm_budget_bytes, precision, max_slots, round_sweeps, stream)
         self.shapes = {}
+        self.inputs = {}
 
     def submit(self, M, N, K, seed, max_iter=300, tol=1e-4, X=None):
         t = did_server_submit(self.h, M, N, K, seed, max_iter, tol, X)
         self.shapes[t] = (M, N, K)
+        if X is not None:
+            self.inputs[t] = X      # read at admission: kept alive until the request finishes
         return t
 
+    def _finished(self, ticket, res):
+        if res["status"] != DID_PENDING:
+            self.inputs.pop(ticket, None)
+        return res
+
     def poll(self, ticket):
-        return did_server_poll(self.h, ticket)
+        return self._finished(ticket, did_server_poll(self.h, ticket))
 
     def wait(self, ticket, timeout_ms=-1):
-        return did_server_wait(self.h, ticket, timeout_ms)
+        return self._finished(ticket, did_server_wait(self.h, ticket, timeout_ms))
 
     def fetch(self, ticket):
         M, N, K = self.shapes[ticket]
@@ -439,8 +447,9 @@ class Server:
 
     def close(self):
         if getattr(self, "h", None):
-            did_server_destroy(self.h)
+            did_server_destroy(self.h)       # finishes every request first
             self.h = None
+            self.inputs = {}
 
     def __enter__(self):
         return self

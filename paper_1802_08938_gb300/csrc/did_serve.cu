@@ -91,6 +91,8 @@ struct did_server {
   double* d_trace = nullptr;
   double* h_trace = nullptr;
   unsigned long long* d_degen = nullptr;
+  unsigned long long* d_bad = nullptr;   // negative or non-finite entries of a request's X
+  unsigned long long* h_bad = nullptr;
   double* d_part = nullptr;          // dense-pass partial sums
   double* h_part = nullptr;
   int dense_grid = 0;
@@ -156,6 +158,11 @@ did_status admit(did_server* s, Req* r) {
   }
   if (e == cudaSuccess && ld > M)
     e = cudaMemset2DAsync(r->X + M, (size_t)ld * 4, 0, (size_t)(ld - M) * 4, (size_t)N, st);
+  // a caller's X must be finite and >= 0, as for did_create
+  if (e == cudaSuccess && r->rq.X) e = cudaMemsetAsync(s->d_bad, 0, sizeof(unsigned long long), st);
+  if (e == cudaSuccess && r->rq.X) e = did::launch_check_nonneg_finite(r->X, (int)M, ld, N, s->d_bad, st);
+  if (e == cudaSuccess && r->rq.X)
+    e = cudaMemcpyAsync(s->h_bad, s->d_bad, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = did::launch_gen_uniform_padded(r->B, (int)M, ld, K, r->rq.seed, 4, st);
   if (e == cudaSuccess) e = did::launch_gen_uniform(r->C, (int64_t)K * N, r->rq.seed, 5, st);
   if (e == cudaSuccess) {
@@ -180,6 +187,7 @@ did_status admit(did_server* s, Req* r) {
     cudaGetLastError();
     return DID_ECUDA;
   }
+  if (r->rq.X && *s->h_bad != 0) return DID_EINVAL;
   double f = 0.0;
   for (int i = 0; i < s->dense_grid; ++i) f += s->h_part[3 * i];
   r->trace.assign(1, 0.5 * f);
@@ -434,6 +442,8 @@ did_status did_server_create(size_t hbm_budget_bytes, did_precision precision, i
   ok = ok && cudaMalloc(&s->d_trace, sizeof(double) * S * round_sweeps) == cudaSuccess;
   ok = ok && cudaMallocHost(&s->h_trace, sizeof(double) * S * round_sweeps) == cudaSuccess;
   ok = ok && cudaMalloc(&s->d_degen, sizeof(unsigned long long) * S) == cudaSuccess;
+  ok = ok && cudaMalloc(&s->d_bad, sizeof(unsigned long long)) == cudaSuccess;
+  ok = ok && cudaMallocHost(&s->h_bad, sizeof(unsigned long long)) == cudaSuccess;
   ok = ok && cudaMalloc(&s->d_part, sizeof(double) * 3 * s->dense_grid) == cudaSuccess;
   ok = ok && cudaMallocHost(&s->h_part, sizeof(double) * 3 * s->dense_grid) == cudaSuccess;
   ok = ok && cudaEventCreate(&s->ev0) == cudaSuccess && cudaEventCreate(&s->ev1) == cudaSuccess;
@@ -571,6 +581,8 @@ void did_server_destroy(did_server* s) {
   cudaFree(s->d_trace);
   cudaFreeHost(s->h_trace);
   cudaFree(s->d_degen);
+  cudaFree(s->d_bad);
+  cudaFreeHost(s->h_bad);
   cudaFree(s->d_part);
   cudaFreeHost(s->h_part);
   if (s->ev0) cudaEventDestroy(s->ev0);

@@ -120,3 +120,36 @@ def test_oversize_rejected(did):
         with pytest.raises(did.DIDError) as e:
             srv.submit(4096, 65536, 8, 1)            # 2 GB of X + R: above the budget
         assert e.value.status == did.DID_E_TOO_LARGE
+
+
+def test_invalid_input_fails_alone(did):
+    """A request whose X has a negative or non-finite entry fails with
+    DID_EINVAL at admission; the requests around it are served as usual, and
+    a caller-supplied X gives the oracle's result."""
+    import torch
+    M, N, K, it = 200, 1500, 6, 10
+    X, _, _ = W.planted(M, N, K, 31, sigma=0.01)
+    Xc = np.ascontiguousarray(X.T).astype(np.float32)       # (N, M) == M x N column-major
+    Xneg = Xc.copy()
+    Xneg[17, 3] = -0.5
+    Xnan = torch.as_tensor(Xc, device="cuda").clone()
+    Xnan[100, 9] = float("nan")
+    with did.Server(4 * GB, max_slots=8, round_sweeps=4) as srv:
+        t_bad = srv.submit(M, N, K, 31, max_iter=it, tol=0.0, X=Xneg)
+        t_ok = srv.submit(M, N, K, 31, max_iter=it, tol=0.0, X=Xc)
+        t_nan = srv.submit(M, N, K, 31, max_iter=it, tol=0.0, X=Xnan)
+        t_gen = srv.submit(300, 2000, 8, 77, max_iter=5, tol=0.0)
+        r_bad, r_ok, r_nan, r_gen = (srv.wait(t) for t in (t_bad, t_ok, t_nan, t_gen))
+        B, C = srv.fetch(t_ok)
+        with pytest.raises(did.DIDError) as e:
+            srv.fetch(t_bad)
+        assert e.value.status == did.DID_EINVAL
+        st = srv.stats()
+    assert r_bad["status"] == did.DID_EINVAL and r_nan["status"] == did.DID_EINVAL
+    assert r_ok["status"] == did.DID_OK and r_gen["status"] == did.DID_OK
+    assert st["failed"] == 2 and st["completed"] == 2
+    B0, C0 = W.init_factors(M, N, K, 31)
+    ref = O.factor(X, B0, C0, order="hals", max_iter=it, stop="none")
+    eB, eC = rel_fro(B, ref["B"]), rel_fro(C, ref["C"])
+    print("caller-supplied X vs oracle: relB %.3g relC %.3g" % (eB, eC))
+    assert eB < 1e-4 and eC < 1e-4
