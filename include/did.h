@@ -165,8 +165,10 @@ typedef struct {
  * legacy default stream, 4 s wait limit. */
 void did_default_options(did_options* opt);
 
-/* Create a factorisation context for X (host or device, M x N column-major).
- * The library copies X to the device, checks it is finite and >= 0
+/* Create a factorisation context for X (host or device, M x N column-major):
+ * the problem min 1/2 ||X - B C||_F^2 s.t. B, C >= 0 of Section 1 (opt:nmf),
+ * columns of X as samples.  The library copies X to the device, checks it is
+ * finite and >= 0
  * (DID_EINVAL otherwise), draws the start point B, C uniform[0,1) from `seed`
  * with the counter-based generator (streams 4 and 5, B[i,k] = word k*M+i,
  * C[k,j] = word k*N+j), and forms R = X - B C.
@@ -186,7 +188,8 @@ did_status did_create_ex(const float* X, int64_t M, int64_t N, int32_t K, uint64
 did_status did_sweep(did_ctx* ctx, int32_t n_sweeps);
 
 /* Sweep until the context's stopping rule holds with tolerance tol, or
- * max_iter sweeps.  *iters_done and *final_obj (may be NULL) receive the
+ * max_iter sweeps: relative change |f_{t-1} - f_t| / f_{t-1} < tol, or the
+ * rule of Section 5, f_t <= tol * f_0 (DID_STOP_PAPER_EPS).  *iters_done and *final_obj (may be NULL) receive the
  * sweep count of this call and the last trace value. */
 did_status did_factor(did_ctx* ctx, int32_t max_iter, double tol, int32_t* iters_done,
                       double* final_obj);
@@ -213,11 +216,12 @@ did_status did_factor(did_ctx* ctx, int32_t max_iter, double tol, int32_t* iters
 did_status did_sweep_static(float* R, int64_t ld, float* B, float* C, int64_t M, int64_t N, int32_t K,
                             int32_t n_sweeps, double* trace, void* stream);
 
-/* Exact objective 1/2 ||X - B C||_F^2 from X, B, C in a fresh pass
- * (float32 products, float64 accumulation); R is not touched. */
+/* Exact objective 1/2 ||X - B C||_F^2 (Section 1) from X, B, C in a fresh
+ * pass (float32 products, float64 accumulation); R is not touched. */
 did_status did_objective(did_ctx* ctx, double* obj);
 
-/* 1/2 ||R||_F^2 of the stored residual (the last trace value). */
+/* 1/2 ||R||_F^2 of the stored residual E = X - B C of Section 4.2 (the
+ * last trace value). */
 did_status did_residual_objective(did_ctx* ctx, double* obj);
 
 /* Recompute R = X - B C densely (Algorithm 3 recomputes e_j := x_j - B c_j)
@@ -229,8 +233,8 @@ did_status did_residual_objective(did_ctx* ctx, double* obj);
  * before the next sweep). */
 did_status did_refresh_residual(did_ctx* ctx);
 
-/* Copy B (M x K column-major) and C (K x N row-major) out; either pointer
- * may be NULL; host or device destinations. */
+/* Copy the factors B (M x K column-major) and C (K x N row-major) of
+ * Section 1 out; either pointer may be NULL; host or device destinations. */
 did_status did_get_factors(did_ctx* ctx, float* B, float* C);
 
 /* Replace B and C (host or device sources, same layouts; must be finite and
@@ -242,13 +246,14 @@ did_status did_set_factors(did_ctx* ctx, const float* B, const float* C);
 /* Copy the stored residual out as float32 M x N column-major (host or device). */
 did_status did_get_residual(did_ctx* ctx, float* R);
 
-/* Copy the objective trace: obj[0] = f at the start point, obj[t] = f after
- * sweep t.  At most cap values are written; *n receives the full length. */
+/* Copy the objective trace (the convergence curve of Section 5): obj[0] = f
+ * at the start point, obj[t] = f after sweep t.  At most cap values are written; *n receives the full length. */
 did_status did_get_trace(did_ctx* ctx, double* obj, int32_t cap, int32_t* n);
 
 did_status did_get_info(did_ctx* ctx, did_info* info);
 
-/* Phase stamps of the last sweep launch (DID_FLAG_PHASE_TIMES): stamps[4*i+p]
+/* Library diagnostics with no counterpart in the paper.
+ * Phase stamps of the last sweep launch (DID_FLAG_PHASE_TIMES): stamps[4*i+p]
  * in nanoseconds for step i = sweep*K + k and phase p (0 b-reduce start, 1
  * after the first grid wait, 2 c-pass end, 3 after the second grid wait).
  * At most cap values are written; *n receives the number recorded. */
@@ -298,7 +303,9 @@ did_status did_generate_uniform(float* out_dev, int64_t n, uint64_t seed, int32_
  * Between rounds, finished requests are retired (B, C copied to host memory
  * owned by the server, device memory freed) and waiting ones admitted, so
  * requests arriving while others run join at the next round.  The start
- * point is the seeded one of did_create; the order is interleaved.
+ * point is the seeded one of did_create; the order is interleaved.  The
+ * paper has no serving layer: each request is the problem of Section 1,
+ * solved by the sweep of did_sweep.
  * All times are seconds on a steady host clock, from server creation.
  * ---------------------------------------------------------------------- */
 typedef struct did_server did_server;
