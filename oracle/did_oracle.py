@@ -15,20 +15,20 @@ the only library step.  Sums follow NumPy's order (the result is exact up to
 rounding order).
 
 Readings of the paper taken here (each is a choice the paper leaves open):
-* A2, zero denominator: when ||c_k||^2 == 0 (resp. ||b_k||^2 == 0) the block
-  b_k (resp. c_k) is left unchanged.  The paper only says the methods can fail
+* Zero denominator (the zero-norm rule): when ||c_k||^2 == 0 (resp.
+  ||b_k||^2 == 0) the block b_k (resp. c_k) is left unchanged.  The paper only says the methods can fail
   when a norm is near zero (Section 5); keeping the block is a valid exact
   minimiser because every value of the block gives the same objective.
-* A7, projection: [z]_+ = z if z > 0 else +0.0 (so -0.0 and NaN map to +0.0).
+* Projection: [z]_+ = z if z > 0 else +0.0 (so -0.0 and NaN map to +0.0).
 * Block orders: ``sweep_hals`` takes b_1 c_1 b_2 c_2 ... (Section 2, HALS);
   ``sweep_dbcd`` takes c_1..c_K then b_1..b_K (Algorithm 2); ``sweep_did``
   is the incremental form with one reduction (Algorithm 3).  The paper states
   that HALS, (D)BCD and DID share their update rules and differ only in the
   order (Section 5, "Correctness").
-* A3, initial scaling (optional): B and C are both multiplied by sqrt(alpha),
+* Initial scaling (optional): B and C are both multiplied by sqrt(alpha),
   alpha = <X, BC> / ||BC||_F^2, the least-squares scale of BC onto X; the
   paper asks for "well scaled initial points" without a formula (Section 5).
-* A4, stopping: relative change |f_{t-1} - f_t| / f_{t-1} < tol, or f_t == 0;
+* Stopping: relative change |f_{t-1} - f_t| / f_{t-1} < tol, or f_t == 0;
   the paper's own rule ||E^t||^2 <= eps ||E^0||^2 (Section 5) is ``paper_eps``.
 * Inner repeats (the acceleration the paper leaves to future work, Section 6,
   in the manner of Gillis & Glineur's accelerated HALS, Neural Computation
@@ -71,7 +71,7 @@ def objective(X, B, C):
 def update_b_hals(A, c, b_old):
     """Minimiser of ||A - b c||_F^2 over b >= 0 (HALS b_k closed form)."""
     cc = float(c @ c)
-    if cc == 0.0:                       # A2: block left unchanged
+    if cc == 0.0:                       # zero-norm rule: block left unchanged
         return np.array(b_old, dtype=np.float64), False
     return project((A @ c) / cc), True
 
@@ -79,7 +79,7 @@ def update_b_hals(A, c, b_old):
 def update_c_hals(A, b, c_old):
     """Minimiser of ||A - b c||_F^2 over c >= 0 (HALS c_k closed form)."""
     bb = float(b @ b)
-    if bb == 0.0:                       # A2
+    if bb == 0.0:                       # zero-norm rule
         return np.array(c_old, dtype=np.float64), False
     return project((b @ A) / bb), True
 
@@ -125,7 +125,7 @@ def _c_step(B, C, E, on_block=None):
         b = B[:, i]
         bb = float(b @ b)
         E += np.outer(b, C[i, :])
-        if bb == 0.0:                   # A2
+        if bb == 0.0:                   # zero-norm rule
             degenerate += 1
         else:
             C[i, :] = project((b @ E) / bb)
@@ -153,7 +153,7 @@ def sweep_dbcd(X, B, C, R=None, on_block=None):
         E += np.outer(B[:, i], c)
         y = E @ c
         z = float(c @ c)
-        if z == 0.0:                    # A2
+        if z == 0.0:                    # zero-norm rule
             degenerate += 1
         else:
             B[:, i] = project(y / z)
@@ -194,7 +194,7 @@ def sweep_did(X, B, C, inner_c=1, inner_b=1):
         dB = np.zeros_like(B)
         for i in range(K):
             vii = V[i, i]
-            if vii == 0.0:                  # A2: b_i unchanged, delta b_i = 0
+            if vii == 0.0:                  # zero-norm rule: b_i unchanged, delta b_i = 0
                 degenerate += 1
                 continue
             s = B[:, i] + W[:, i] / vii
@@ -209,7 +209,7 @@ def sweep_did(X, B, C, inner_c=1, inner_b=1):
 
 
 def init_scale(X, B, C):
-    """A3: scale B and C by sqrt(alpha), alpha = <X, BC> / ||BC||_F^2."""
+    """Initial scaling: B and C times sqrt(alpha), alpha = <X, BC> / ||BC||_F^2."""
     B = np.asarray(B, np.float64)
     C = np.asarray(C, np.float64)
     P = B @ C

@@ -219,7 +219,7 @@ def test_factor_stopping_rule(did):
 
 
 def test_degenerate_zero_row(did):
-    """A zero row of C leaves b_k unchanged and is counted (reading A2)."""
+    """A zero row of C leaves b_k unchanged and is counted (the zero-norm rule)."""
     X, M, N, K = W.make("planted_uniform_200x1000_k10", seed=7, M=50, N=80, K=3)
     B0, C0 = W.init_factors(M, N, K, 7)
     C0[1, :] = 0.0

@@ -256,7 +256,7 @@ def test_equivariance(order):
 
 
 def test_degenerate_blocks_left_unchanged():
-    """A2: a zero row of C keeps b_k; a b_k projected to zero keeps c_k."""
+    """Zero-norm rule: a zero row of C keeps b_k; a b_k projected to zero keeps c_k."""
     rs = np.random.default_rng(4)
     X, B, C = _rand_problem(rs, 6, 8, 3)
     C[1, :] = 0.0
@@ -271,7 +271,7 @@ def test_degenerate_blocks_left_unchanged():
 
 
 def test_init_scale_is_least_squares_scale():
-    """A3: alpha = <X,BC>/||BC||^2 is the least-squares scale (library lstsq)."""
+    """Initial scaling: alpha = <X,BC>/||BC||^2 is the least-squares scale (library lstsq)."""
     rs = np.random.default_rng(2)
     X, B, C = _rand_problem(rs, 8, 10, 3)
     Bs, Cs = O.init_scale(X, B, C)
