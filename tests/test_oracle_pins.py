@@ -168,7 +168,7 @@ def test_kkt_after_block_update(seed):
 # ----------------------------------------------------------------- invariants
 @pytest.mark.parametrize("order", ["hals", "dbcd"])
 def test_monotone_and_residual_invariant(order):
-    """P2: f never increases after a block step. P3: kept R == X - BC."""
+    """Monotone: f never increases after a block step.  Kept residual: R == X - BC."""
     rs = np.random.default_rng(7)
     X, B, C = _rand_problem(rs, 30, 40, 5)
     fs = [O.objective(X, B, C)]
@@ -189,7 +189,7 @@ def test_monotone_and_residual_invariant(order):
 
 
 def test_did_equals_dbcd_literal_form():
-    """P4: Algorithm 3 (W, V, delta b) equals DBCD with a kept residual."""
+    """Incremental form: Algorithm 3 (W, V, delta b) equals DBCD with a kept residual."""
     rs = np.random.default_rng(11)
     X, B, C = _rand_problem(rs, 25, 60, 6)
     B1, C1, R1 = B.copy(), C.copy(), None
@@ -214,7 +214,7 @@ def test_same_iteration_count_did_dbcd():
 # -------------------------------------------------------------- special cases
 @pytest.mark.parametrize("seed", range(3))
 def test_rank_one_recovered_in_one_sweep(seed):
-    """P5: K = 1, X = u v^T with u, v > 0: one HALS sweep reaches f = 0."""
+    """Exact rank-one recovery: K = 1, X = u v^T with u, v > 0: one HALS sweep reaches f = 0."""
     rs = np.random.default_rng(seed)
     u, v = rs.uniform(0.1, 1, 17), rs.uniform(0.1, 1, 23)
     X = np.outer(u, v)
@@ -225,7 +225,7 @@ def test_rank_one_recovered_in_one_sweep(seed):
 
 @pytest.mark.parametrize("order", ["hals", "dbcd", "did"])
 def test_exact_factorisation_is_fixed_point(order):
-    """P6: with X = B0 C0 and start (B0, C0), a sweep changes nothing."""
+    """Fixed point: with X = B0 C0 and start (B0, C0), a sweep changes nothing."""
     rs = np.random.default_rng(5)
     B0, C0 = rs.uniform(0, 1, (9, 4)), rs.uniform(0, 1, (4, 13))
     X = B0 @ C0
@@ -236,7 +236,7 @@ def test_exact_factorisation_is_fixed_point(order):
 
 @pytest.mark.parametrize("order", ["hals", "dbcd", "did"])
 def test_equivariance(order):
-    """P7: permuting columns of X permutes C; permuting rows permutes B;
+    """Equivariance: permuting columns of X permutes C; permuting rows permutes B;
     scaling X and the start of B by a scales B only."""
     rs = np.random.default_rng(9)
     X, B, C = _rand_problem(rs, 11, 14, 3)
