@@ -146,17 +146,37 @@ def status_string(s):
     return _lib.did_status_string(int(s)).decode()
 
 
-def _ptr(a):
-    """Address of a tensor's / array's first element (None passes NULL)."""
-    if a is None:
-        return None
-    if hasattr(a, "data_ptr"):
-        return a.data_ptr()
-    if isinstance(a, np.ndarray):
-        return a.ctypes.data
-    if isinstance(a, int):
+def _buf(a, n, what, dtype="float32"):
+    """Address of a buffer the library reads or writes n elements of, after
+    checking that it is a dense array of that dtype with at least n elements
+    (a raw integer address is passed as it is; None passes NULL).  A failed
+    check raises DIDError(DID_EINVAL) before the library is called."""
+    if a is None or isinstance(a, int):
         return a
-    raise TypeError("expected a torch tensor, NumPy array or address, got %r" % type(a))
+    n = max(0, int(n))
+    if hasattr(a, "data_ptr"):
+        import torch
+        want = torch.float32 if dtype == "float32" else torch.float64
+        dense = a.is_contiguous() or (a.dim() == 2 and a.t().is_contiguous())
+        ok_type, size = a.dtype == want, a.numel()
+    elif isinstance(a, np.ndarray):
+        dense = a.flags.c_contiguous or a.flags.f_contiguous
+        ok_type, size = a.dtype == np.dtype(dtype), a.size
+    else:
+        raise TypeError("%s: expected a torch tensor, NumPy array or address, got %r" % (what, type(a)))
+    if not ok_type:
+        raise DIDError(DID_EINVAL, "%s: expected %s elements, got %s" % (what, dtype, a.dtype))
+    if not dense:
+        raise DIDError(DID_EINVAL, "%s: expected a dense (contiguous) buffer" % what)
+    if size < n:
+        raise DIDError(DID_EINVAL, "%s: %d elements, the call needs %d" % (what, size, n))
+    return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+
+
+# (M, N, K) of each live context and of each served request, for the checks
+# of the buffers passed to the calls that take only a handle (or a ticket).
+_CTX_SHAPE = {}
+_TICKET_SHAPE = {}
 
 
 def _stream_of(stream):
@@ -186,11 +206,13 @@ def default_options():
 # ------------------------------------------------------------ C-named calls
 def did_create(X, M, N, K, seed, options=None):
     h = ctypes.c_void_p()
+    x = _buf(X, max(0, M) * max(0, N), "X")
     if options is None:
-        st = _lib.did_create(_ptr(X), M, N, K, seed, ctypes.byref(h))
+        st = _lib.did_create(x, M, N, K, seed, ctypes.byref(h))
     else:
-        st = _lib.did_create_ex(_ptr(X), M, N, K, seed, ctypes.byref(options), ctypes.byref(h))
+        st = _lib.did_create_ex(x, M, N, K, seed, ctypes.byref(options), ctypes.byref(h))
     _check(st)
+    _CTX_SHAPE[h.value] = (M, N, K)
     return h
 
 
@@ -203,7 +225,9 @@ def did_sweep(h, n):
 
 def did_sweep_static(R, ld, B, C, M, N, K, n_sweeps, trace=None, stream=None):
     """Sweeps on caller-owned device buffers with no device allocation."""
-    _check(_lib.did_sweep_static(_ptr(R), ld, _ptr(B), _ptr(C), M, N, K, n_sweeps, _ptr(trace),
+    ldn, Nn, Kn = max(0, ld), max(0, N), max(0, K)
+    _check(_lib.did_sweep_static(_buf(R, ldn * Nn, "R"), ld, _buf(B, ldn * Kn, "B"), _buf(C, Kn * Nn, "C"),
+                                 M, N, K, n_sweeps, _buf(trace, n_sweeps, "trace", "float64"),
                                  _stream_of(stream)))
 
 
@@ -230,16 +254,23 @@ def did_refresh_residual(h):
     _check(_lib.did_refresh_residual(h), h)
 
 
+def _shape_of(h):
+    return _CTX_SHAPE.get(h.value if hasattr(h, "value") else h, (0, 0, 0))
+
+
 def did_get_factors(h, B, C):
-    _check(_lib.did_get_factors(h, _ptr(B), _ptr(C)), h)
+    M, N, K = _shape_of(h)
+    _check(_lib.did_get_factors(h, _buf(B, M * K, "B"), _buf(C, K * N, "C")), h)
 
 
 def did_set_factors(h, B, C):
-    _check(_lib.did_set_factors(h, _ptr(B), _ptr(C)), h)
+    M, N, K = _shape_of(h)
+    _check(_lib.did_set_factors(h, _buf(B, M * K, "B"), _buf(C, K * N, "C")), h)
 
 
 def did_get_residual(h, R):
-    _check(_lib.did_get_residual(h, _ptr(R)), h)
+    M, N, K = _shape_of(h)
+    _check(_lib.did_get_residual(h, _buf(R, M * N, "R")), h)
 
 
 def did_get_trace(h):
@@ -266,21 +297,24 @@ def did_get_phase_times(h):
 
 
 def did_destroy(h):
+    _CTX_SHAPE.pop(h.value if hasattr(h, "value") else h, None)
     _lib.did_destroy(h)
 
 
 def did_generate_planted(X_dev, M, N, K, seed, coords=0, zero_frac=0.0, sigma=0.0, salt_frac=0.0,
                          salt_value=5.0, stream=None):
-    _check(_lib.did_generate_planted(_ptr(X_dev), M, N, K, seed, coords, zero_frac, sigma, salt_frac,
+    _check(_lib.did_generate_planted(_buf(X_dev, max(0, M) * max(0, N), "X"), M, N, K, seed, coords, zero_frac,
+                                     sigma, salt_frac,
                                      salt_value, _stream_of(stream)))
 
 
 def did_generate_image(X_dev, M, N, seed, zero_frac=0.8, stream=None):
-    _check(_lib.did_generate_image(_ptr(X_dev), M, N, seed, zero_frac, _stream_of(stream)))
+    _check(_lib.did_generate_image(_buf(X_dev, max(0, M) * max(0, N), "X"), M, N, seed, zero_frac,
+                                   _stream_of(stream)))
 
 
 def did_generate_uniform(out_dev, n, seed, stream_id, stream=None):
-    _check(_lib.did_generate_uniform(_ptr(out_dev), n, seed, stream_id, _stream_of(stream)))
+    _check(_lib.did_generate_uniform(_buf(out_dev, n, "out"), n, seed, stream_id, _stream_of(stream)))
 
 
 def did_server_create(hbm_budget_bytes, precision=DID_FP32, max_slots=64, round_sweeps=4, stream=None):
@@ -293,9 +327,10 @@ def did_server_create(hbm_budget_bytes, precision=DID_FP32, max_slots=64, round_
 
 
 def did_server_submit(h, M, N, K, seed, max_iter, tol, X=None):
-    r = did_request(_ptr(X), M, N, K, seed, max_iter, tol)
+    r = did_request(_buf(X, max(0, M) * max(0, N), "X"), M, N, K, seed, max_iter, tol)
     t = ctypes.c_uint64()
     _check(_lib.did_server_submit(h, ctypes.byref(r), ctypes.byref(t)))
+    _TICKET_SHAPE[(h.value, t.value)] = (M, N, K)
     return t.value
 
 
@@ -317,7 +352,9 @@ def did_server_wait(h, ticket, timeout_ms=-1):
 
 
 def did_server_fetch(h, ticket, B, C):
-    _check(_lib.did_server_fetch(h, ticket, _ptr(B), _ptr(C)))
+    M, N, K = _TICKET_SHAPE.get((h.value, ticket), (0, 0, 0))
+    _check(_lib.did_server_fetch(h, ticket, _buf(B, M * K, "B"), _buf(C, K * N, "C")))
+    _TICKET_SHAPE.pop((h.value, ticket), None)      # results are released once fetched
 
 
 def did_server_stats(h):
@@ -327,6 +364,8 @@ def did_server_stats(h):
 
 
 def did_server_destroy(h):
+    for key in [k for k in _TICKET_SHAPE if k[0] == h.value]:
+        del _TICKET_SHAPE[key]
     _lib.did_server_destroy(h)
 
 
@@ -341,7 +380,8 @@ class Context:
         o = default_options()
         o.precision, o.order, o.refresh_every, o.stop = precision, order, refresh_every, stop
         o.init_scale, o.grid_ctas = int(bool(init_scale)), grid_ctas
-        o.B_init, o.C_init = _ptr(B_init), _ptr(C_init)
+        o.B_init = _buf(B_init, max(0, M) * max(0, K), "B_init")
+        o.C_init = _buf(C_init, max(0, K) * max(0, N), "C_init")
         o.stream = _stream_of(stream)
         o.timeout_ns, o.debug_barrier_extra, o.flags = timeout_ns, debug_barrier_extra, flags
         o.inner_c, o.inner_b = inner_c, inner_b
