@@ -325,6 +325,9 @@ def run_reference(args):
     value = (1.0 / sec) * cols / w["N"]
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value,
+            "ms_per_step_kind": "extrapolated: measured on a %d-column slice, scaled linearly in N to %d columns"
+                                % (cols, w["N"]),
+            "ms_per_step_measured_slice": 1000.0 * sec,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": args.workload, "M": w["M"], "N": w["N"], "K": w["K"],
                                             "precision": "fp64 oracle"},
@@ -577,6 +580,13 @@ def main():
                     "frac": achieved / peak, "traffic": traffic if args.order == "interleaved" else None,
                     "kernel": "sweep_kernel", "peak_kind": peak_kind,
                     "alg_bytes_per_sweep": float(passes) * M * N * s_bytes,
+                    # the survey's per-sweep figure, one read and one write of R per k; the
+                    # deferred write-back moves fewer bytes, and frac above uses the bytes it moves
+                    "alg_bytes_per_sweep_2KMNs": 2.0 * K * M * N * s_bytes,
+                    "frac_on_2KMNs": (2.0 * K * M * N * s_bytes * args.steps / (kms / 1000.0) / 1e9) / peak,
+                    "bytes_note": ("frac counts the %d passes of R a sweep moves (%s write-back); on 2K = %d "
+                                   "passes the same kernel time gives frac_on_2KMNs"
+                                   % (passes, "deferred" if info1["lazy_writeback"] else "eager", 2 * K)),
                     "lazy_writeback": int(info1["lazy_writeback"]), "ring_stages": int(info1["ring_stages"]),
                     "kernel_ms_per_sweep": kms / max(1, args.steps)}
 

@@ -208,11 +208,17 @@ did_status did_factor(did_ctx* ctx, int32_t max_iter, double tol, int32_t* iters
  * Its scratch (grid partials, per-CTA scalars, control words) is one static
  * device array of 6 MiB that every GPU which loads the library holds until
  * the process exits; limits: ld <= 8192, n_sweeps <= 1024, at most 160 CTAs
- * (DID_E_TOO_LARGE beyond them).  It calls no cudaMalloc/cudaFree.  The first
- * call on a device looks up that device's address of the array, so make it
- * before any stream capture.  All calls share the array: calls that overlap
- * on the GPU (other streams, other threads) race and must be serialised by
- * the caller.  Synchronises `stream` (NULL = legacy default stream). */
+ * (DID_E_TOO_LARGE beyond them).  It calls no cudaMalloc/cudaFree.  R, B and
+ * C must be device memory of the current device (or managed memory): a host
+ * or unregistered pointer returns DID_EINVAL before anything is launched.
+ * The first call on a device looks up that device's address of the array;
+ * make that first call before any stream capture begins.  All calls share the
+ * array: calls that overlap on the GPU (other streams, other threads) race
+ * and must be serialised by the caller.  Synchronises `stream` (NULL = legacy
+ * default stream).  DID_ETIMEOUT (a bounded device wait ran out) leaves R, B
+ * and C partly updated, so R need not equal X - B C any more; this call has
+ * no X, so the caller must rebuild R itself.  trace then receives only the
+ * sweeps that completed. */
 did_status did_sweep_static(float* R, int64_t ld, float* B, float* C, int64_t M, int64_t N, int32_t K,
                             int32_t n_sweeps, double* trace, void* stream);
 

@@ -8,7 +8,10 @@ passed by pointer and must use the C ABI layouts:
 
 * X: M x N column-major == a C-contiguous (N, M) array, or an F-contiguous (M, N) one
 * B: M x K column-major == C-contiguous (K, M), or F-contiguous (M, K)
-* C: K x N row-major    == C-contiguous (K, N)
+* C: K x N row-major    == C-contiguous (K, N), or F-contiguous (N, K)
+
+A 2-D array of another shape (for instance X as a C-contiguous (M, N) array,
+which would be read transposed) is refused with DIDError(DID_EINVAL).
 
 There is no CPU fallback: importing this package without the built library
 raises ImportError (build it with ``__graft_entry__.build()`` or
@@ -146,30 +149,41 @@ def status_string(s):
     return _lib.did_status_string(int(s)).decode()
 
 
-def _buf(a, n, what, dtype="float32"):
+def _buf(a, n, what, dtype="float32", mem=None):
     """Address of a buffer the library reads or writes n elements of, after
     checking that it is a dense array of that dtype with at least n elements
-    (a raw integer address is passed as it is; None passes NULL).  A failed
-    check raises DIDError(DID_EINVAL) before the library is called."""
+    (a raw integer address is passed as it is; None passes NULL).  With
+    mem = (outer, inner), a 2-D array must also have the memory order the C
+    ABI wants: C-contiguous of shape (outer, inner), or its transpose in
+    Fortran order (shape (inner, outer)).  So an M x N column-major matrix
+    (mem = (N, M)) given as a C-contiguous (M, N) array is refused rather
+    than read transposed.  A failed check raises DIDError(DID_EINVAL) before
+    the library is called."""
     if a is None or isinstance(a, int):
         return a
     n = max(0, int(n))
     if hasattr(a, "data_ptr"):
         import torch
         want = torch.float32 if dtype == "float32" else torch.float64
-        dense = a.is_contiguous() or (a.dim() == 2 and a.t().is_contiguous())
-        ok_type, size = a.dtype == want, a.numel()
+        c_order = a.is_contiguous()
+        f_order = a.dim() == 2 and a.t().is_contiguous()
+        ok_type, size, shape = a.dtype == want, a.numel(), tuple(a.shape)
     elif isinstance(a, np.ndarray):
-        dense = a.flags.c_contiguous or a.flags.f_contiguous
-        ok_type, size = a.dtype == np.dtype(dtype), a.size
+        c_order, f_order = a.flags.c_contiguous, a.ndim == 2 and a.flags.f_contiguous
+        ok_type, size, shape = a.dtype == np.dtype(dtype), a.size, a.shape
     else:
         raise TypeError("%s: expected a torch tensor, NumPy array or address, got %r" % (what, type(a)))
     if not ok_type:
         raise DIDError(DID_EINVAL, "%s: expected %s elements, got %s" % (what, dtype, a.dtype))
-    if not dense:
+    if not (c_order or f_order):
         raise DIDError(DID_EINVAL, "%s: expected a dense (contiguous) buffer" % what)
     if size < n:
         raise DIDError(DID_EINVAL, "%s: %d elements, the call needs %d" % (what, size, n))
+    if mem is not None and len(shape) == 2:
+        outer, inner = (int(v) for v in mem)
+        if not ((c_order and shape == (outer, inner)) or (f_order and shape == (inner, outer))):
+            raise DIDError(DID_EINVAL, "%s: expected a C-contiguous %s array (or its transpose in Fortran "
+                                       "order), got shape %s" % (what, (outer, inner), shape))
     return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
 
 
@@ -206,7 +220,7 @@ def default_options():
 # ------------------------------------------------------------ C-named calls
 def did_create(X, M, N, K, seed, options=None):
     h = ctypes.c_void_p()
-    x = _buf(X, max(0, M) * max(0, N), "X")
+    x = _buf(X, max(0, M) * max(0, N), "X", mem=(N, M))
     if options is None:
         st = _lib.did_create(x, M, N, K, seed, ctypes.byref(h))
     else:
@@ -226,7 +240,8 @@ def did_sweep(h, n):
 def did_sweep_static(R, ld, B, C, M, N, K, n_sweeps, trace=None, stream=None):
     """Sweeps on caller-owned device buffers with no device allocation."""
     ldn, Nn, Kn = max(0, ld), max(0, N), max(0, K)
-    _check(_lib.did_sweep_static(_buf(R, ldn * Nn, "R"), ld, _buf(B, ldn * Kn, "B"), _buf(C, Kn * Nn, "C"),
+    _check(_lib.did_sweep_static(_buf(R, ldn * Nn, "R", mem=(N, ld)), ld, _buf(B, ldn * Kn, "B", mem=(K, ld)),
+                                 _buf(C, Kn * Nn, "C", mem=(K, N)),
                                  M, N, K, n_sweeps, _buf(trace, n_sweeps, "trace", "float64"),
                                  _stream_of(stream)))
 
@@ -260,17 +275,17 @@ def _shape_of(h):
 
 def did_get_factors(h, B, C):
     M, N, K = _shape_of(h)
-    _check(_lib.did_get_factors(h, _buf(B, M * K, "B"), _buf(C, K * N, "C")), h)
+    _check(_lib.did_get_factors(h, _buf(B, M * K, "B", mem=(K, M)), _buf(C, K * N, "C", mem=(K, N))), h)
 
 
 def did_set_factors(h, B, C):
     M, N, K = _shape_of(h)
-    _check(_lib.did_set_factors(h, _buf(B, M * K, "B"), _buf(C, K * N, "C")), h)
+    _check(_lib.did_set_factors(h, _buf(B, M * K, "B", mem=(K, M)), _buf(C, K * N, "C", mem=(K, N))), h)
 
 
 def did_get_residual(h, R):
     M, N, K = _shape_of(h)
-    _check(_lib.did_get_residual(h, _buf(R, M * N, "R")), h)
+    _check(_lib.did_get_residual(h, _buf(R, M * N, "R", mem=(N, M))), h)
 
 
 def did_get_trace(h):
@@ -303,13 +318,14 @@ def did_destroy(h):
 
 def did_generate_planted(X_dev, M, N, K, seed, coords=0, zero_frac=0.0, sigma=0.0, salt_frac=0.0,
                          salt_value=5.0, stream=None):
-    _check(_lib.did_generate_planted(_buf(X_dev, max(0, M) * max(0, N), "X"), M, N, K, seed, coords, zero_frac,
+    _check(_lib.did_generate_planted(_buf(X_dev, max(0, M) * max(0, N), "X", mem=(N, M)), M, N, K, seed, coords,
+                                     zero_frac,
                                      sigma, salt_frac,
                                      salt_value, _stream_of(stream)))
 
 
 def did_generate_image(X_dev, M, N, seed, zero_frac=0.8, stream=None):
-    _check(_lib.did_generate_image(_buf(X_dev, max(0, M) * max(0, N), "X"), M, N, seed, zero_frac,
+    _check(_lib.did_generate_image(_buf(X_dev, max(0, M) * max(0, N), "X", mem=(N, M)), M, N, seed, zero_frac,
                                    _stream_of(stream)))
 
 
@@ -327,7 +343,7 @@ def did_server_create(hbm_budget_bytes, precision=DID_FP32, max_slots=64, round_
 
 
 def did_server_submit(h, M, N, K, seed, max_iter, tol, X=None):
-    r = did_request(_buf(X, max(0, M) * max(0, N), "X"), M, N, K, seed, max_iter, tol)
+    r = did_request(_buf(X, max(0, M) * max(0, N), "X", mem=(N, M)), M, N, K, seed, max_iter, tol)
     t = ctypes.c_uint64()
     _check(_lib.did_server_submit(h, ctypes.byref(r), ctypes.byref(t)))
     _TICKET_SHAPE[(h.value, t.value)] = (M, N, K)
@@ -353,7 +369,7 @@ def did_server_wait(h, ticket, timeout_ms=-1):
 
 def did_server_fetch(h, ticket, B, C):
     M, N, K = _TICKET_SHAPE.get((h.value, ticket), (0, 0, 0))
-    _check(_lib.did_server_fetch(h, ticket, _buf(B, M * K, "B"), _buf(C, K * N, "C")))
+    _check(_lib.did_server_fetch(h, ticket, _buf(B, M * K, "B", mem=(K, M)), _buf(C, K * N, "C", mem=(K, N))))
     _TICKET_SHAPE.pop((h.value, ticket), None)      # results are released once fetched
 
 
@@ -380,8 +396,8 @@ class Context:
         o = default_options()
         o.precision, o.order, o.refresh_every, o.stop = precision, order, refresh_every, stop
         o.init_scale, o.grid_ctas = int(bool(init_scale)), grid_ctas
-        o.B_init = _buf(B_init, max(0, M) * max(0, K), "B_init")
-        o.C_init = _buf(C_init, max(0, K) * max(0, N), "C_init")
+        o.B_init = _buf(B_init, max(0, M) * max(0, K), "B_init", mem=(K, M))
+        o.C_init = _buf(C_init, max(0, K) * max(0, N), "C_init", mem=(K, N))
         o.stream = _stream_of(stream)
         o.timeout_ns, o.debug_barrier_extra, o.flags = timeout_ns, debug_barrier_extra, flags
         o.inner_c, o.inner_b = inner_c, inner_b

@@ -50,6 +50,7 @@ struct Req {
   did_status status = DID_PENDING;
   int ld = 0;
   size_t bytes = 0;
+  bool reserved = false;   // bytes counted in the server's budget ledger
   void* block = nullptr;
   float *X = nullptr, *B = nullptr, *C = nullptr, *P = nullptr, *bold = nullptr;
   void* R = nullptr;
@@ -194,11 +195,18 @@ did_status admit(did_server* s, Req* r) {
   return DID_OK;
 }
 
+// Give back a request's device memory and its share of the budget.  The
+// share is returned even when the allocation itself failed (admission
+// reserves it before allocating), so a failed admission never shrinks the
+// budget left for the requests behind it.
 void release(did_server* s, Req* r) {
   if (r->block) {
     cudaFreeAsync(r->block, s->stream);
     r->block = nullptr;
+  }
+  if (r->reserved) {
     s->used -= r->bytes;
+    r->reserved = false;
   }
 }
 
@@ -327,6 +335,7 @@ void worker_main(did_server* s) {
       if (s->used + r->bytes > s->budget) break;
       s->queue.pop_front();
       s->used += r->bytes;
+      r->reserved = true;
       s->peak = std::max(s->peak, s->used);
       r->t_start = now_s(s->t0);
       lk.unlock();

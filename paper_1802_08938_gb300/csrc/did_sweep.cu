@@ -285,6 +285,25 @@ extern "C" did_status did_sweep_static(float* R, int64_t ld, float* B, float* C,
       n_sweeps < 0 || ((uintptr_t)R & 15) || ((uintptr_t)B & 15))
     return DID_EINVAL;
   if (ld > kStaticMaxLd || n_sweeps > kStaticMaxSweeps) return DID_E_TOO_LARGE;
+  // R, B and C must be device memory of the current device (or managed
+  // memory): a host address would reach the kernel as a global address.
+  {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+      cudaGetLastError();
+      return DID_ECUDA;
+    }
+    const void* bufs[3] = {R, B, C};
+    for (const void* q : bufs) {
+      cudaPointerAttributes at{};
+      if (cudaPointerGetAttributes(&at, q) != cudaSuccess) {
+        cudaGetLastError();
+        return DID_EINVAL;
+      }
+      const bool on_device = at.type == cudaMemoryTypeDevice && at.device == dev;
+      if (!on_device && at.type != cudaMemoryTypeManaged) return DID_EINVAL;
+    }
+  }
   static_assert(sizeof(g_static_scratch) >= (size_t)5 << 20, "scratch holds the grid partials");
   const StaticLayout L = static_layout();
   if (L.end > kStaticScratchBytes) return DID_E_TOO_LARGE;
@@ -337,9 +356,16 @@ extern "C" did_status did_sweep_static(float* R, int64_t ld, float* B, float* C,
   }
   Ctrl h{};
   if (cudaMemcpyAsync(&h, base + L.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      (trace && n_sweeps > 0 &&
-       cudaMemcpyAsync(trace, base + L.trace, sizeof(double) * n_sweeps, cudaMemcpyDefault, s) != cudaSuccess) ||
       cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return DID_ECUDA;
+  }
+  // Only the sweeps this call completed have trace values; the rest of the
+  // window still holds an earlier call's.
+  const int done = h.err != 0 ? std::max(0, std::min(h.sweeps, n_sweeps)) : n_sweeps;
+  if (trace && done > 0 &&
+      (cudaMemcpyAsync(trace, base + L.trace, sizeof(double) * done, cudaMemcpyDefault, s) != cudaSuccess ||
+       cudaStreamSynchronize(s) != cudaSuccess)) {
     cudaGetLastError();
     return DID_ECUDA;
   }

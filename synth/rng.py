@@ -3,8 +3,9 @@
 This module holds no arithmetic of the factorisation method.  It defines one
 counter-based generator and the distributions the workloads draw from; the
 CUDA library carries its own, separately written implementation of the same
-definition (``paper_1802_08938_gb300/csrc/did_gen.cu``) so that very large
-inputs can be generated on the device.
+definition (``paper_1802_08938_gb300/csrc/did_internal.cuh`` for the
+generator, ``paper_1802_08938_gb300/csrc/did_dense.cu`` for the device
+workload kernels) so that very large inputs can be generated on the device.
 
 Definition (the contract both implementations follow):
 

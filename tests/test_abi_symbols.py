@@ -106,14 +106,10 @@ def test_invalid_options_rejected_before_any_cuda_call(lib, change):
 STRUCTS = ["did_options", "did_info", "did_request", "did_result", "did_server_stats_t"]
 
 
-def c_struct_layout(tmp_path, did):
+def c_struct_layout(tmp_path, did, cc):
     """sizeof and field offsets of every public struct, as a C compiler lays
     them out from include/did.h (host ABI)."""
-    import shutil
     import subprocess
-    cc = shutil.which("gcc") or shutil.which("cc")
-    if cc is None:
-        pytest.skip("no C compiler")
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "did.h"', "int main(void) {"]
     for s in STRUCTS:
         lines.append('  printf("%s sizeof %%zu\\n", sizeof(%s));' % (s, s))
@@ -123,14 +119,14 @@ def c_struct_layout(tmp_path, did):
     src = tmp_path / "layout.c"
     src.write_text("\n".join(lines))
     exe = tmp_path / "layout"
-    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    subprocess.run(cc + ["-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
     return {tuple(line.split()[:2]): int(line.split()[2]) for line in out.splitlines()}
 
 
-def test_struct_layouts_match_the_header(tmp_path):
+def test_struct_layouts_match_the_header(tmp_path, c_compiler):
     import paper_1802_08938_gb300 as did
-    layout = c_struct_layout(tmp_path, did)
+    layout = c_struct_layout(tmp_path, did, c_compiler)
     for s in STRUCTS:
         cls = getattr(did, s)
         assert layout[(s, "sizeof")] == ctypes.sizeof(cls), s

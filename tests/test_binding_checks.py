@@ -84,3 +84,28 @@ def test_static_sweep_and_generators_check_sizes(did):
         did.did_generate_uniform(np.zeros(9, np.float32), 10, 1, 0)
     with pytest.raises(did.DIDError):
         did.did_generate_image(np.zeros((N, M - 1), np.float32), M, N, 1)
+
+
+def test_transposed_layout_is_refused(did):
+    """X is M x N column-major: a C-contiguous (M, N) array would be read
+    transposed, so it is refused; (N, M) C-contiguous and (M, N) Fortran-order
+    pass.  The same holds for B (M x K column-major) and C (K x N row-major)."""
+    M, N, K = 6, 9, 2
+    with pytest.raises(did.DIDError) as e:
+        did.Context(np.ones((M, N), np.float32), M, N, K)
+    assert e.value.status == did.DID_EINVAL
+    assert did._buf(np.ones((N, M), np.float32), M * N, "X", mem=(N, M)) is not None
+    assert did._buf(np.asfortranarray(np.ones((M, N), np.float32)), M * N, "X", mem=(N, M)) is not None
+    X = np.ones((N, M), np.float32)
+    with pytest.raises(did.DIDError) as e:
+        did.Context(X, M, N, K, B_init=np.ones((M, K), np.float32))      # B as row-major M x K
+    assert e.value.status == did.DID_EINVAL
+    with pytest.raises(did.DIDError) as e:
+        did.Context(X, M, N, K, C_init=np.ones((N, K), np.float32))      # C as column-major K x N
+    assert e.value.status == did.DID_EINVAL
+    torch = pytest.importorskip("torch")
+    with pytest.raises(did.DIDError):
+        did._buf(torch.ones((M, N)), M * N, "X", mem=(N, M))
+    with pytest.raises(did.DIDError):
+        did._buf(torch.ones((M, N)).t(), M * N, "X", mem=(N, M))     # (N, M) view of row-major (M, N) memory
+    assert did._buf(torch.ones((N, M)).t(), M * N, "X", mem=(N, M)) is not None

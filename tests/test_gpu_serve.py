@@ -153,3 +153,29 @@ def test_invalid_input_fails_alone(did):
     eB, eC = rel_fro(B, ref["B"]), rel_fro(C, ref["C"])
     print("caller-supplied X vs oracle: relB %.3g relC %.3g" % (eB, eC))
     assert eB < 1e-4 and eC < 1e-4
+
+
+def test_failed_admission_returns_its_budget(did):
+    """A request larger than the GPU's memory (but within the budget) fails
+    with DID_ENOMEM when its allocation is refused.  Its share of the budget
+    must come back: the next request fits the budget only then, and admission
+    is first come, first served, so a lost share would hold it forever."""
+    import torch
+    free, total = torch.cuda.mem_get_info()
+    big = (4096, 11_000_000, 8)
+    small = (4096, 500_000, 8)
+    est = lambda m, n, k: m * n * 8 + k * n * 4 + m * k * 4      # X, R (float32), C, B
+    if est(*big) <= total:
+        pytest.skip("the GPU has more memory than the large request needs")
+    budget = est(*big) + est(*small) // 2       # the small one fits only after the large one left
+    with did.Server(budget, max_slots=4, round_sweeps=2) as srv:
+        t_big = srv.submit(*big, 1, max_iter=2, tol=0.0)
+        t_small = srv.submit(*small, 2, max_iter=2, tol=0.0)
+        r_big = srv.wait(t_big, timeout_ms=120000)
+        r_small = srv.wait(t_small, timeout_ms=120000)
+        st = srv.stats()
+    print("large request: status %d; small request: status %d, %d sweeps" % (r_big["status"], r_small["status"],
+                                                                           r_small["iters"]))
+    assert r_big["status"] == did.DID_ENOMEM
+    assert r_small["status"] == did.DID_OK and r_small["iters"] == 2
+    assert st["failed"] == 1 and st["completed"] == 1
