@@ -249,36 +249,40 @@ def order_bench(did, X, M, N, K, w, seed, stream, order, steps, warmup, flags=0,
     f = c.objective()
     trace = c.trace()
     c.close()
-    out = {"order": order, "gemm": "bf16x9 emulation" if flags & did.DID_FLAG_GEMM_BF16X9 else "float32 SIMT",
-           "writeback": "eager" if flags & did.DID_FLAG_EAGER_WRITEBACK else "deferred",
+    out = {"order": order, "writeback": "eager" if flags & did.DID_FLAG_EAGER_WRITEBACK else "deferred",
            "inner": list(inner), "trace": [float(v) for v in trace],
            "value": steps / (ms / 1000.0), "unit": "sweeps/s", "ms_per_sweep": ms / steps,
            "objective_after": f, "sweeps": warmup + steps,
            "sweep_ms": (i1["sweep_kernel_ms"] - i0["sweep_kernel_ms"]) / steps}
     if order == "did_batched":
-        out["roofline"] = batched_roofline(M, N, K, out["sweep_ms"], bool(flags & did.DID_FLAG_GEMM_BF16X9))
+        out["roofline"] = batched_roofline(M, N, K, out["sweep_ms"])
     return out
 
 
-def batched_roofline(M, N, K, ms_per_sweep, bf16x9):
-    """Whole-sweep roofline of the batched order: float32 SIMT FMA peak for the
-    pedantic GEMMs; for the BF16x9 emulation, nine bfloat16 products per float32
-    product against the measured bfloat16 tensor peak (sustained)."""
+def batched_roofline(M, N, K, ms_per_sweep):
+    """Whole-sweep roofline of the batched order: its three passes of R (the g
+    pass reads R, the update pass reads and writes it) against the measured
+    copy bandwidth, with the tensor-core work beside it (six bfloat16 products
+    per float32 product, against the measured sustained bfloat16 peak)."""
+    peak, kind = measured_peaks()
+    alg = 3.0 * M * N * 4
+    gbs = alg / (ms_per_sweep / 1e3) / 1e9
     fl = batched_flops(M, N, K)
-    tf = fl / (ms_per_sweep / 1e3) / 1e12
-    if not bf16x9:
-        return {"bound": "alu", "achieved": tf, "peak": FP32_SIMT_TFLOPS, "unit": "TFLOP/s",
-                "frac": tf / FP32_SIMT_TFLOPS, "flops_per_sweep": fl,
-                "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
-                "note": "whole sweep (cuBLAS SGEMMs + solve/update/norm kernels)"}
-    peak, kind = 1700.0, "fallback"
+    tpeak = 1700.0
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         with open(p) as f:
-            peak, kind = float(json.load(f)["bf16_tflops_sustained"]), "measured (sustained)"
-    return {"bound": "tensor", "achieved": 9 * tf, "peak": peak, "unit": "TFLOP/s (bf16 products)",
-            "frac": 9 * tf / peak, "flops_per_sweep": fl, "peak_kind": kind,
-            "note": "whole sweep; float32 flops x 9 bfloat16 products of the BF16x9 emulation"}
+            tpeak = float(json.load(f)["bf16_tflops_sustained"])
+    tf6 = 6 * fl / (ms_per_sweep / 1e3) / 1e12
+    return {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+            "peak_kind": peak_kind_note(kind), "alg_bytes_per_sweep": alg,
+            "passes_of_R": 3, "tensor_tflops_bf16x6": tf6, "tensor_frac_of_sustained_bf16": tf6 / tpeak,
+            "flops_per_sweep_f32": fl,
+            "note": "whole sweep: g pass (reads R), update pass (reads and writes R), solves and the B step"}
+
+
+def peak_kind_note(kind):
+    return kind
 
 
 def sweep_passes(K, lazy):
@@ -352,8 +356,6 @@ def main():
     ap.add_argument("--order", default="interleaved", choices=sorted(ORDERS),
                     help="block order of the main line: per-k interleaved (Section 4.1), per-k C-first "
                          "(Algorithm 2), or the batched form of Algorithm 3")
-    ap.add_argument("--gemm", default="pedantic", choices=["pedantic", "bf16x9"],
-                    help="GEMMs of the batched order: float32 SIMT or cuBLAS BF16x9 emulation")
     ap.add_argument("--eager", action="store_true",
                     help="interleaved order: write R after every k (no deferred write-back)")
     ap.add_argument("--no-orders", action="store_true",
@@ -423,8 +425,6 @@ def main():
     flags = did.DID_FLAG_PHASE_TIMES if args.phases else 0
     if args.eager:
         flags |= did.DID_FLAG_EAGER_WRITEBACK
-    if args.order == "did_batched" and args.gemm == "bf16x9":
-        flags |= did.DID_FLAG_GEMM_BF16X9
     ctx = did.Context(X, M, N, K, seed=seed, precision=prec, order=ORDERS[args.order],
                       refresh_every=w["refresh_every"], init_scale=w["init_scale"], stream=stream, flags=flags)
     for _ in range(args.warmup):
@@ -519,20 +519,21 @@ def main():
 
     orders = None
     if not args.no_orders and prec == did.DID_FP32 and args.order == "interleaved":
-        x9 = did.DID_FLAG_GEMM_BF16X9
+        batched_ok = K <= 64
+        runs = [("interleaved", did.DID_FLAG_EAGER_WRITEBACK, (1, 1)), ("did", 0, (1, 1))]
+        if batched_ok:
+            runs += [("did_batched", 0, (1, 1)), ("did_batched", 0, (2, 2)), ("did_batched", 0, (4, 4))]
         orders = [order_bench(did, X, M, N, K, w, seed, stream, o, args.steps, args.warmup, f, r)
-                  for o, f, r in (("interleaved", did.DID_FLAG_EAGER_WRITEBACK, (1, 1)), ("did", 0, (1, 1)),
-                                  ("did_batched", 0, (1, 1)), ("did_batched", x9, (1, 1)),
-                                  ("did_batched", x9, (2, 2)), ("did_batched", x9, (4, 4)))]
+                  for o, f, r in runs]
         # inner repeats: sweeps (and time) to reach the objective that plain batched sweeps reach
-        target = orders[3]["trace"][-1]
+        target = orders[2]["trace"][-1] if batched_ok else orders[1]["trace"][-1]
         for o in orders:
             o["ratio_vs_main"] = o["value"] / value
             hit = [i for i, v in enumerate(o.pop("trace")) if v <= target]
             o["sweeps_to_plain_final"] = hit[0] if hit else None
             o["ms_to_plain_final"] = hit[0] * o["ms_per_sweep"] if hit else None
-        # the batched form runs 4 of the library's kernels per sweep next to cuBLAS SGEMMs
-        other_launches += 2 * args.steps + 4 * 4 * args.steps
+        # the per-k orders launch one sweep kernel per sweep; the batched order 8 kernels per sweep
+        other_launches += 2 * args.steps + (3 * 8 * args.steps if batched_ok else 0)
 
     e2e = None
     if not args.no_e2e:
@@ -573,7 +574,7 @@ def main():
         cpu = cpu_baseline(args.workload)
 
     if args.order == "did_batched":
-        roofline = batched_roofline(M, N, K, kms / max(1, args.steps), args.gemm == "bf16x9")
+        roofline = batched_roofline(M, N, K, kms / max(1, args.steps))
         roofline.update({"traffic": None, "kernel": "batched sweep", "kernel_ms_per_sweep": kms / max(1, args.steps)})
     else:
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -603,7 +604,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == did.DID_FP32 else "bf16-storage/f32",
             "data": "synthetic",
             "config": {"workload": args.workload, "M": M, "N": N, "K": K, "precision": args.precision,
-                       "order": args.order, "gemm": args.gemm if args.order == "did_batched" else None,
+                       "order": args.order,
                        "refresh_every": w["refresh_every"], "init_scale": w["init_scale"],
                        "l2": "inputs larger than L2 (R is %.1f GB)" % (M * N * s_bytes / 1e9),
                        "parallelism": "replicas" if ws > 1 else "single"},

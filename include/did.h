@@ -64,10 +64,14 @@ typedef enum { DID_FP32 = 0, DID_BF16R = 1 } did_precision;
  *   residual by one rank-2K product, then takes W = E C^T and V = C C^T in a
  *   single reduction and applies b_i := [b_i + w_i/v_ii - sum_{k<i}
  *   (v_ik/v_ii) delta b_k]_+; the delta b correction of R is applied lazily
- *   by the next sweep.  Float32 residual only, K <= 128 (did_create_ex
- *   returns DID_EINVAL otherwise).  The objective of each sweep is the
- *   float64 norm of the residual after the C step, with the B step's change
- *   taken from an exact float64 identity in W, V and delta b. */
+ *   by the next sweep.  Float32 residual only, K <= 64 (did_create_ex
+ *   returns DID_EINVAL otherwise).  The products run on the tensor cores as
+ *   TF32x3 (each float32 operand split into a TF32 part and a remainder,
+ *   three products accumulated in float32), in two passes over R per sweep:
+ *   one forms g, one applies the rank-2K update and forms W.  The objective
+ *   of each sweep is the float64 norm of the residual after the C step, with
+ *   the B step's change taken from an exact float64 identity in W, V and
+ *   delta b. */
 typedef enum { DID_ORDER_INTERLEAVED = 0, DID_ORDER_DID = 1, DID_ORDER_DID_BATCHED = 2 } did_order;
 
 /* Stopping rule of did_factor.
@@ -107,14 +111,6 @@ typedef struct {
  * the tensor-core pass (BF16x3 for a bfloat16 residual with K <= 128, TF32x3
  * for a float32 one with K <= 64; larger K always takes the SIMT pass). */
 #define DID_FLAG_SIMT_REFRESH 2
-/* did_options.flags (DID_ORDER_DID_BATCHED only): run the sweep's float32
- * GEMMs through cuBLAS's float32 emulation on the bfloat16 tensor cores (each
- * operand split into three bfloat16 terms, all nine products accumulated in
- * float32) instead of pedantic float32 SIMT arithmetic.  The emulation has a
- * large fixed cost per GEMM: it is faster only when M and K are large (on one
- * GB300, 1.5x at 5000 x 200000 with K = 50, 7x slower at 784 x 70000 with
- * K = 16). */
-#define DID_FLAG_GEMM_BF16X9 4
 /* did_options.flags (DID_ORDER_INTERLEAVED): deferred write-back defers the
  * write of R for k to the pass for k+1 (one write per pair of k, three passes
  * over R per pair instead of four).  It needs two more M-vectors of shared

@@ -33,7 +33,6 @@ DID_ORDER_INTERLEAVED, DID_ORDER_DID, DID_ORDER_DID_BATCHED = 0, 1, 2
 DID_STOP_RELCHANGE, DID_STOP_PAPER_EPS = 0, 1
 DID_FLAG_PHASE_TIMES = 1
 DID_FLAG_SIMT_REFRESH = 2
-DID_FLAG_GEMM_BF16X9 = 4
 DID_FLAG_EAGER_WRITEBACK = 8
 DID_FLAG_LAZY_WRITEBACK = 16
 DID_FLAG_SINGLE_COLUMNS = 32

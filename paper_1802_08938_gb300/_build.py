@@ -68,9 +68,8 @@ def build(force=False, verbose=False, ptxas_v=False):
                 sys.stderr.write(log)
     objs = [o for o, _ in results]
     tmp = LIB + ".tmp"
-    libdir = os.path.join(os.path.dirname(os.path.dirname(cc)), "lib64")
-    cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart=static", "-L" + libdir, "-lcublas",
-           "-Xlinker", "-rpath=" + libdir]
+    # the CUDA runtime is linked statically; no other library is needed
+    cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart=static"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))

@@ -365,7 +365,7 @@ int chunk_size(const did_ctx* c, int64_t remaining) {
   return (int)std::max<int64_t>(1, chunk);
 }
 
-// Batched order: sweeps of GEMMs and small kernels on the context's stream.
+// Batched order: sweeps of the batched kernels on the context's stream.
 did_status run_batched(did_ctx* c, int64_t max_sweeps, int stop_rule, double tol, int64_t* done_total) {
   *done_total = 0;
   while (*done_total < max_sweeps) {
@@ -375,17 +375,29 @@ did_status run_batched(did_ctx* c, int64_t max_sweeps, int stop_rule, double tol
     }
     const int chunk = chunk_size(c, max_sweeps - *done_total);
     const int n = stop_rule ? 1 : chunk;     // with a stopping rule: one sweep per check
+    const uint64_t tmo = c->opt.timeout_ns ? c->opt.timeout_ns : kDefaultTimeoutNs;
+    int* err = did::batched_error_word(c->batched);
     DID_CUDA(c, cudaEventRecord(c->ev0, c->stream));
     for (int s = 0; s < n; ++s)
       DID_CUDA(c, did::batched_sweep(c->batched, (float*)c->R, c->Y, c->C, c->ld, c->N, c->K, c->opt.inner_c,
-                                     c->opt.inner_b, c->degen, c->trace_dev + s, c->stream));
+                                     c->opt.inner_b, c->degen, tmo, c->trace_dev + s, c->stream));
     DID_CUDA(c, cudaEventRecord(c->ev1, c->stream));
     DID_CUDA(c, cudaMemcpyAsync(c->trace_host, c->trace_dev, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+    DID_CUDA(c, cudaMemcpyAsync(&c->ctrl_host->err, err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     DID_CUDA(c, cudaStreamSynchronize(c->stream));
     float ms = 0.f;
     DID_CUDA(c, cudaEventElapsedTime(&ms, c->ev0, c->ev1));
     c->sweep_ms += ms;
     c->sweep_launches += n;
+    if (c->ctrl_host->err != 0) {
+      // A bounded wait of a tensor-core pass ran out: the sweeps of this chunk
+      // are not trusted; the residual is recomputed before the next sweep.
+      const int e = c->ctrl_host->err;
+      DID_CUDA(c, cudaMemsetAsync(err, 0, sizeof(int), c->stream));
+      c->need_refresh = true;
+      return fail(c, DID_ETIMEOUT, "a bounded wait of the batched sweep ran out (device error %d); "
+                  "the residual will be recomputed", e);
+    }
     bool stopped = false;
     for (int s = 0; s < n; ++s) {
       const double f = c->trace_host[s];
@@ -515,10 +527,12 @@ static did_status create_impl(did_ctx* c, const float* X, uint64_t seed) {
   }
 #undef ALLOC
   if (c->opt.order == DID_ORDER_DID_BATCHED) {
-    st = dev_alloc(c, &p, did::batched_workspace_bytes(c->ld, N, K));
+    const size_t wsb = did::batched_workspace_bytes(c->ld, N, K);
+    if (wsb == 0) return fail(c, DID_EINVAL, "the batched order supports K <= 64");
+    st = dev_alloc(c, &p, wsb);
     if (st != DID_OK) return st;
-    c->batched = did::batched_create(p, c->ld, N, K, (c->opt.flags & DID_FLAG_GEMM_BF16X9) != 0, c->stream);
-    if (!c->batched) return fail(c, DID_ECUDA, "cuBLAS handle creation failed");
+    c->batched = did::batched_create(p, c->ld, N, K, c->stream);
+    if (!c->batched) return fail(c, DID_ECUDA, "batched-order set-up failed");
   }
   st = host_alloc(c, &p, sizeof(Ctrl));
   if (st != DID_OK) return st;
@@ -582,7 +596,7 @@ did_status did_create_ex(const float* X, int64_t M, int64_t N, int32_t K, uint64
       (o.order != DID_ORDER_INTERLEAVED && o.order != DID_ORDER_DID && o.order != DID_ORDER_DID_BATCHED) ||
       (o.order == DID_ORDER_DID_BATCHED && (o.precision != DID_FP32 || !did::batched_supported(K))) ||
       (o.stop != DID_STOP_RELCHANGE && o.stop != DID_STOP_PAPER_EPS) || o.refresh_every < 0 ||
-      o.debug_barrier_extra < 0 || (o.flags & ~(DID_FLAG_PHASE_TIMES | DID_FLAG_SIMT_REFRESH | DID_FLAG_GEMM_BF16X9 | DID_FLAG_EAGER_WRITEBACK |
+      o.debug_barrier_extra < 0 || (o.flags & ~(DID_FLAG_PHASE_TIMES | DID_FLAG_SIMT_REFRESH | DID_FLAG_EAGER_WRITEBACK |
                    DID_FLAG_LAZY_WRITEBACK | DID_FLAG_SINGLE_COLUMNS)) ||
       ((o.flags & DID_FLAG_EAGER_WRITEBACK) && (o.flags & DID_FLAG_LAZY_WRITEBACK)) ||
       o.inner_c < 0 || o.inner_c > 64 || o.inner_b < 0 || o.inner_b > 64 ||

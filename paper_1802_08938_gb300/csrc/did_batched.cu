@@ -1,10 +1,11 @@
-// DID in its batched form (Algorithm 3): one reduction per sweep.
+// DID in its batched form (Algorithm 3): one reduction per sweep, on the
+// library's own tensor-core kernels.
 //
 // The C-first sweep of Algorithms 2/3 visits c_1..c_K with B fixed, then
-// b_1..b_K with C fixed.  Its batched form on the GPU keeps a stored residual
-// R_s and a pending rank-K correction D (the delta b of the last B step):
-// the true residual is E = R_s - D C.  One sweep is
-//   C step   g   = B^T E = B^T R_s - (B^T D) C               (GEMMs)
+// b_1..b_K with C fixed.  Its batched form keeps a stored residual R_s and a
+// pending rank-K correction D (the delta b of the last B step): the true
+// residual is E = R_s - D C.  One sweep is
+//   C step   g   = B^T E = B^T R_s - (B^T D) C
 //            per column j, i = 1..K in order (equations up:c with the
 //            residual kept implicitly through G = B^T B):
 //              t_i = g_ij - sum_{l<i} G_il dl_l ;  c_ij' = [c_ij + t_i / G_ii]_+
@@ -20,104 +21,921 @@
 // repeats, the residual after them is still E - B dl (C step) and E' - db C'
 // (B step), so a repeat needs g, G, W and V only -- no pass over R.
 // The objective of the sweep: ||E'||^2 = ||R_s||^2 right after the rank-2K
-// update (a deterministic norm pass), then the B step's change from an exact
-// identity in float64:
-//   ||E''||^2 = ||E'||^2 - 2 sum_{m,i} db_i[m] W[m,i] + sum_{i,k} (D^T D)_ik V_ik
-// (carrying ||E'||^2 itself from sweep to sweep through the C step's identity
-// ||E'||^2 = ||E||^2 - 2 sum_j g_j.dl_j + sum_j dl_j^T G dl_j would accumulate
-// the float32 rounding of g over the sweeps).  A dense refresh re-anchors
-// R_s = X - B C and D = 0.
+// update (summed in the epilogue of that pass), then the B step's change from
+// an exact identity in float64:
+//   ||E''||^2 = ||E'||^2 - 2 sum_{m,i} db_i[m] W[m,i] + sum_{i,k} (D^T D)_ik V_ik.
+// A dense refresh re-anchors R_s = X - B C and D = 0.
 //
-// The large products are plain GEMMs and use cuBLAS (float32 SGEMM, or its
-// BF16x9 emulation); the sequential solves, the norm and the objective are
-// the kernels below.
-#include "did_internal.cuh"
+// Every product runs on the tensor cores as BF16x6: each float32 operand is
+// split into three bfloat16 terms (tc::split_bf16x3) and the six partial
+// products whose terms reach 2^-18 of the leading one are accumulated in
+// float32, which matches float32 arithmetic (the residual is updated in
+// place for many sweeps, so its products need float32 accuracy; a TF32x3
+// split, about 2^-20 per product, let the residual drift by 4.5e-5 of the
+// objective in 20 sweeps on a near-exact fit).
+//
+// Kernels of one sweep (K <= 64):
+//   prep_gb     B -> bfloat16 x3 tiles of 32 rows for the g pass (1 MB at K = 50)
+//   g_kernel    tcgen05: g^T = R_s^T B over column tiles of up to 256 columns.
+//               R_s arrives by 2-D TMA (128-byte swizzle) in chunks of 32 rows;
+//               eight warps split each chunk into its three bfloat16 terms in
+//               tensor memory (the A operand), and one thread issues the six
+//               products.  One read of R_s.
+//   solve_c     per column: g_j - (B^T D) c_j, the K successive c updates,
+//               C', the operand tiles [C_old; dl] and C'^T (bfloat16 x3) of
+//               the next pass, and per-block partials of V = C' C'^T.
+//   update      tcgen05, persistent over (128-row block, column range) units:
+//               the row block of Y = [D B] (bfloat16 x3) stays in tensor
+//               memory; per 32- or 64-column tile, acc = Y Z, E' = R_s - acc
+//               (read by TMA, written back by one TMA store), ||E'||^2, and
+//               E' (bfloat16 x3, into tensor memory) times C'^T accumulated
+//               into the unit's W rows in tensor memory.  One read and one
+//               write of R_s.
+//   vreduce, update_b, yy, objective: the small K x K and per-row steps.
+// So a sweep moves three passes of R_s (two reads, one write); a single pass
+// would need a column's g (all M rows) before its update, and the W rows of
+// every row block, on chip at once.
+//
+// Every mbarrier wait is bounded; on expiry the kernel records the error,
+// stops issuing work, waits (bounded) for its copies and MMAs, frees its
+// tensor memory and returns; the host reads the error word after the sweeps.
+#include "did_tc.cuh"
 
-#include <cublas_v2.h>
 #include <stdio.h>
+
+#include <algorithm>
 
 namespace did {
 
 namespace {
 
-constexpr int kMaxK = 128;
+constexpr int kMaxK = 64;             // tensor-memory budget of the update pass
+constexpr int kTcThreads = 384;       // warp 0 producer, warp 1 MMA, 2-3 idle, 4-11 split / epilogue
+constexpr int kWorkWarps = 8;
+constexpr int kGStages = 3;
+constexpr int kGChunk = 32;           // rows of R_s per g stage (128 bytes of a column)
+constexpr uint32_t kTmemCols = 512;
+// Both tensor-core kernels take all 512 TMEM columns, so two of their CTAs
+// must never share an SM: every launch asks for more than half of an SM's
+// shared memory.
+constexpr size_t kMinSmem = 120 * 1024;
 constexpr int kSolveThreads = 128;
 constexpr int kBThreads = 128;
+constexpr int kNormPartMax = 1024;
+
+// Element (r, c) of a bfloat16 operand tile in the no-swizzle K-major
+// core-matrix layout with contraction length kp (a multiple of 16): core
+// matrix (r/8, c/8) at ((r/8) * (kp/8) + c/8) * 64 elements, element
+// (r%8, c%8) inside it.  Core matrices are 128 bytes apart along K and
+// kp * 16 bytes apart along M/N.
+__host__ __device__ __forceinline__ size_t tiled2(int r, int c, int kp) {
+  return ((size_t)(r >> 3) * (size_t)(kp >> 3) + (size_t)(c >> 3)) * 64 + (size_t)((r & 7) * 8 + (c & 7));
+}
+
+// The six products (i, j), i + j <= 2, of two three-term splits.
+__constant__ const int kProdA[6] = {0, 0, 1, 0, 1, 2};
+__constant__ const int kProdB[6] = {0, 1, 0, 2, 1, 0};
+constexpr int kProds = 6;
+
+// Three bfloat16 terms of v, packed in pairs along K: word w of term p holds
+// elements 2w (low half) and 2w + 1 (high half).
+__device__ __forceinline__ void split_pair(float v0, float v1, uint32_t& w0, uint32_t& w1, uint32_t& w2) {
+  __nv_bfloat16 a0, a1, a2, b0, b1, b2;
+  tc::split_bf16x3(v0, a0, a1, a2);
+  tc::split_bf16x3(v1, b0, b1, b2);
+  w0 = tc::pack_bf16x2(a0, b0);
+  w1 = tc::pack_bf16x2(a1, b1);
+  w2 = tc::pack_bf16x2(a2, b2);
+}
+
+__device__ __forceinline__ unsigned char* align1024(unsigned char* p) {
+  const uint32_t a = smem_u32(p);
+  return p + (((a + 1023u) & ~1023u) - a);
+}
+
+// ------------------------------------------------------------------- plan
+struct BPlan {
+  int M, ld, K, KN, Z16;  // KN = K rounded up to 16 (N of the g and W products); Z16 = 2K rounded up to 16
+  int64_t N;
+  // g pass
+  int nt;                 // columns per g tile (<= 256)
+  int64_t gtiles;
+  int mchunks;            // ceil(ld / 32)
+  int ggrid;
+  size_t gstage, gsmem;
+  // update pass
+  int nu;                 // columns per update tile (32 or 64)
+  int64_t utiles;
+  int RB, Q, units, ugrid, ustages;
+  size_t ustage, usmem;
+  // solve
+  int sgrid, npairs;
+};
+
+int sm_count() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
+}
+
+size_t al1024(size_t x) { return (x + 1023) & ~(size_t)1023; }
+
+bool make_plan(int ld, int64_t N, int K, BPlan* p) {
+  if (K < 1 || K > kMaxK) return false;
+  const int sms = sm_count();
+  BPlan P{};
+  P.ld = ld;
+  P.N = N;
+  P.K = K;
+  P.KN = (K + 15) / 16 * 16;
+  P.Z16 = (2 * K + 15) / 16 * 16;
+  // g pass: tiles of nt <= 256 columns, as many as fill whole waves of the grid
+  const int64_t waves = std::max<int64_t>(1, (N + (int64_t)sms * 256 - 1) / ((int64_t)sms * 256));
+  int64_t nt = (N + waves * sms - 1) / (waves * sms);
+  nt = (nt + 15) / 16 * 16;
+  P.nt = (int)std::min<int64_t>(256, std::max<int64_t>(16, nt));
+  P.gtiles = (N + P.nt - 1) / P.nt;
+  P.mchunks = (ld + kGChunk - 1) / kGChunk;
+  P.ggrid = (int)std::min<int64_t>(sms, P.gtiles);
+  P.gstage = al1024((size_t)P.nt * 128 + (size_t)P.KN * 192);
+  P.gsmem = std::max(kMinSmem, kGStages * P.gstage + (size_t)P.KN * 256 * 4 + 1024 + 256);
+  // update pass: 64-column tiles where tensor memory holds them, else 32
+  // (columns: two accumulators, two E' buffers of three terms, W, three Y terms)
+  auto tmem_cols = [&](int nu) { return 2 * nu + 3 * nu + P.KN + 3 * P.Z16 / 2; };
+  P.nu = tmem_cols(64) <= (int)kTmemCols ? 64 : 32;
+  if (tmem_cols(P.nu) > (int)kTmemCols) return false;
+  P.utiles = (N + P.nu - 1) / P.nu;
+  P.RB = (ld + 127) / 128;
+  // column ranges per row block: whole waves of units, every range >= 1 tile
+  int bestQ = 1;
+  double best = -1.0;
+  const int qmax = (int)std::min<int64_t>(P.utiles, std::max(1, 8 * sms / P.RB + 1));
+  for (int Q = 1; Q <= qmax; ++Q) {
+    const int64_t units = (int64_t)P.RB * Q;
+    const int64_t w = (units + sms - 1) / sms;
+    const double eff = (double)units / (double)(w * std::min<int64_t>(sms, units)) *
+                       ((double)P.utiles / Q) / (double)((P.utiles + Q - 1) / Q);
+    const double score = eff - (units < sms ? 0.5 * (1.0 - (double)units / sms) : 0.0);
+    if (score > best + 1e-9) {
+      best = score;
+      bestQ = Q;
+    }
+    if (units >= sms && eff >= 0.97) {
+      bestQ = Q;
+      break;
+    }
+  }
+  P.Q = bestQ;
+  P.units = P.RB * P.Q;
+  P.ugrid = std::min(sms, P.units);
+  const size_t fixed = 1024 + 512 + (size_t)P.KN * 128 * 4;   // alignment, barriers, W running sums
+  P.ustage = al1024((size_t)P.nu * 128 * 4 + (size_t)3 * P.nu * P.Z16 * 2 + (size_t)3 * P.KN * P.nu * 2);
+  P.ustages = 0;
+  for (int s = 4; s >= 2; --s)
+    if (s * P.ustage + fixed <= 227 * 1024) {
+      P.ustages = s;
+      break;
+    }
+  if (P.ustages == 0) return false;
+  P.usmem = std::max(kMinSmem, P.ustages * P.ustage + fixed);
+  P.sgrid = 2 * sms;
+  P.npairs = K * (K + 1) / 2;
+  *p = P;
+  return true;
+}
+
+// ------------------------------------------------------------- prep_gb
+// B (ld x K column-major) -> [chunk][term][KN x 32] bfloat16 tiles for the g
+// pass: rows of the operand are k (the N of the product), the contraction is
+// the chunk's 32 rows of B.
+__global__ void prep_gb_kernel(const float* __restrict__ B, int M, int ld, int K, int KN, int mchunks,
+                               __nv_bfloat16* __restrict__ out) {
+  const int64_t n = (int64_t)mchunks * KN * kGChunk;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int ml = (int)(idx % kGChunk);
+    const int k = (int)((idx / kGChunk) % KN);
+    const int mc = (int)(idx / ((int64_t)kGChunk * KN));
+    const int m = mc * kGChunk + ml;
+    const float v = (m < M && k < K) ? B[(size_t)k * ld + m] : 0.f;
+    __nv_bfloat16 p0, p1, p2;
+    tc::split_bf16x3(v, p0, p1, p2);
+    __nv_bfloat16* base = out + (size_t)mc * 3 * KN * kGChunk;
+    const size_t o = tiled2(k, ml, kGChunk);
+    base[o] = p0;
+    base[(size_t)KN * kGChunk + o] = p1;
+    base[(size_t)2 * KN * kGChunk + o] = p2;
+  }
+}
+
+// -------------------------------------------------------------- g pass
+struct GArgs {
+  const __nv_bfloat16* Bg;   // [mchunks][3][KN x 32] tiles
+  float* g;          // [N][K]: g_j contiguous
+  int* err;
+  int ld, K, KN, nt, mchunks;
+  int64_t N, gtiles;
+  size_t gstage;
+  uint64_t timeout_ns;
+};
+
+enum { G_FULL = 0, G_EMPTY = kGStages, G_SREADY = 2 * kGStages, G_SFREE = G_SREADY + 2, G_ACCFULL = G_SFREE + 2,
+       G_ACCEMPTY = G_ACCFULL + 2, G_DRAIN = G_ACCEMPTY + 2, G_NBARS };
+
+// Chunks of one accumulation group: the tensor cores sum a group's products
+// in a TMEM accumulator, and the split warps add the group totals in float32
+// (round to nearest) in shared memory.  Short accumulator chains keep the
+// tensor core's own float32 accumulation, which does not round to nearest,
+// from biasing g over M rows.
+constexpr int kGGroup = 4;
+
+__global__ void __launch_bounds__(kTcThreads, 1) g_kernel(GArgs a, const __grid_constant__ CUtensorMap tmR) {
+  extern __shared__ unsigned char sm_raw[];
+  unsigned char* sm = align1024(sm_raw);
+  float* gsum = reinterpret_cast<float*>(sm + kGStages * a.gstage);          // [KN][256] running sums
+  uint64_t* bars = reinterpret_cast<uint64_t*>(gsum + (size_t)a.KN * 256);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + G_NBARS);
+  int* shared_flags = reinterpret_cast<int*>(tmem_slot + 4);   // [0] MMA chunks issued
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int KN = a.KN;
+  const size_t rbytes = (size_t)a.nt * 128;
+  if (threadIdx.x == 0) {
+    shared_flags[0] = 0;
+    for (int i = 0; i < G_NBARS; ++i) {
+      const bool per_warp = i == G_SREADY || i == G_SREADY + 1 || i == G_ACCEMPTY || i == G_ACCEMPTY + 1;
+      mbar_init(bars + i, per_warp ? kWorkWarps : 1);
+    }
+  }
+  fence_mbar_init();
+  if (warp == 1) tc::tmem_alloc(tmem_slot, kTmemCols);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = *tmem_slot;
+  // TMEM columns: accumulator set x (of alternate groups), half h at
+  // 2KN x + KN h; staging buffer b at 4KN + 96 b, half h at +48 h, term p at
+  // +16 p (32 bfloat16 rows in 16 columns).
+  auto accum = [&](int x, int h) { return (uint32_t)(2 * KN * x + KN * h); };
+  auto staging = [&](int b, int h) { return (uint32_t)(4 * KN + 96 * b + 48 * h); };
+
+  const int64_t ntile = a.gtiles > blockIdx.x ? (a.gtiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t total = ntile * a.mchunks;
+  const int ngroups = (a.mchunks + kGGroup - 1) / kGGroup;   // per tile
+  int* err = a.err;
+  const uint64_t tmo = a.timeout_ns;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int64_t c = 0;
+      for (; c < total; ++c) {
+        const int64_t ti = c / a.mchunks;
+        const int mc = (int)(c % a.mchunks);
+        const int64_t tile = blockIdx.x + ti * gridDim.x;
+        const int s = (int)(c % kGStages);
+        if (c >= kGStages && !tc::wait(bars + G_EMPTY + s, (uint32_t)(((c / kGStages) - 1) & 1), err, tmo)) break;
+        unsigned char* st = sm + (size_t)s * a.gstage;
+        mbar_arrive_expect_tx(bars + G_FULL + s, (uint32_t)(rbytes + (size_t)KN * 192));
+        tc::tma_load_2d(st, &tmR, mc * kGChunk, (int)(tile * a.nt), bars + G_FULL + s);
+        bulk_load(st + rbytes, a.Bg + (size_t)mc * 3 * KN * kGChunk, (uint32_t)KN * 192, bars + G_FULL + s);
+      }
+      // copies still in flight complete before the CTA exits (bounded)
+      for (int64_t d = std::max<int64_t>(0, c - kGStages); d < c; ++d)
+        mbar_wait_bounded(bars + G_FULL + (d % kGStages), (uint32_t)((d / kGStages) & 1), err, tmo);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = tc::instr_desc_bf16(128, KN);
+      int64_t c = 0;
+      for (; c < total; ++c) {
+        const int64_t ti = c / a.mchunks;
+        const int mc = (int)(c % a.mchunks);
+        const int64_t gi = ti * ngroups + mc / kGGroup;          // group index in this CTA's stream
+        const int x = (int)(gi & 1);
+        const bool gfirst = mc % kGGroup == 0;
+        const bool glast = mc % kGGroup == kGGroup - 1 || mc == a.mchunks - 1;
+        const int s = (int)(c % kGStages), b = (int)(c & 1);
+        if (!tc::wait(bars + G_FULL + s, (uint32_t)((c / kGStages) & 1), err, tmo)) break;
+        if (!tc::wait(bars + G_SREADY + b, (uint32_t)((c >> 1) & 1), err, tmo)) break;
+        if (gfirst && gi >= 2 && !tc::wait(bars + G_ACCEMPTY + x, (uint32_t)(((gi >> 1) - 1) & 1), err, tmo)) break;
+        tc::fence_after();
+        const uint32_t sB = smem_u32(sm + (size_t)s * a.gstage + rbytes);
+        for (int h = 0; h < 2; ++h) {
+          if (h * 128 >= a.nt) break;
+          for (int pr = 0; pr < kProds; ++pr) {
+            const uint32_t acol = staging(b, h) + (uint32_t)(16 * kProdA[pr]);
+            const uint32_t boff = (uint32_t)(kProdB[pr] * KN * kGChunk * 2);
+            for (int kk = 0; kk < kGChunk / 16; ++kk) {
+              const uint64_t bd = tc::smem_desc(sB + boff + (uint32_t)kk * 256u, 128u, (uint32_t)kGChunk * 16u);
+              tc::mma_bf16_tmem_a(tmem + accum(x, h), tmem + acol + (uint32_t)kk * 8u, bd, idesc,
+                                  (!gfirst || pr > 0 || kk > 0) ? 1u : 0u);
+            }
+          }
+        }
+        tc::mma_commit(bars + G_EMPTY + s);
+        tc::mma_commit(bars + G_SFREE + b);
+        if (glast) tc::mma_commit(bars + G_ACCFULL + x);
+      }
+      shared_flags[0] = (int)std::min<int64_t>(c, 1 << 30);
+    }
+  } else if (warp >= 4) {
+    const int sw = warp - 4;
+    const int quarter = warp & 3, half = sw >> 2;
+    const int jl = half * 128 + quarter * 32 + lane;     // column within the tile (TMEM lane jl % 128)
+    const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+    bool ok = true;
+    for (int64_t c = 0; c < total && ok; ++c) {
+      const int64_t ti = c / a.mchunks;
+      const int mc = (int)(c % a.mchunks);
+      const int64_t tile = blockIdx.x + ti * gridDim.x;
+      const int64_t gi = ti * ngroups + mc / kGGroup;
+      const int x = (int)(gi & 1);
+      const bool glast = mc % kGGroup == kGGroup - 1 || mc == a.mchunks - 1;
+      const int s = (int)(c % kGStages), b = (int)(c & 1);
+      ok = tc::wait(bars + G_FULL + s, (uint32_t)((c / kGStages) & 1), err, tmo);
+      if (ok && c >= 2) ok = tc::wait(bars + G_SFREE + b, (uint32_t)(((c >> 1) - 1) & 1), err, tmo);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) break;
+      tc::fence_after();
+      // Row jl of the swizzled tile: logical 16-byte chunk q sits at chunk q ^ (jl % 8).
+      uint32_t t0[16], t1[16], t2[16];
+      const unsigned char* row = sm + (size_t)s * a.gstage + (size_t)jl * 128;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (jl < a.nt) v = *reinterpret_cast<const float4*>(row + ((q ^ (jl & 7)) << 4));
+        split_pair(v.x, v.y, t0[2 * q], t1[2 * q], t2[2 * q]);
+        split_pair(v.z, v.w, t0[2 * q + 1], t1[2 * q + 1], t2[2 * q + 1]);
+      }
+      const uint32_t col = staging(b, half);
+      tc::tmem_st_u16(tmem + lane_base + col, t0);
+      tc::tmem_st_u16(tmem + lane_base + col + 16, t1);
+      tc::tmem_st_u16(tmem + lane_base + col + 32, t2);
+      tc::tmem_st_wait();
+      tc::fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bars + G_SREADY + b);
+      if (glast) {
+        // the group's total into the running sums of this column (the first
+        // group of a tile starts them)
+        ok = tc::wait(bars + G_ACCFULL + x, (uint32_t)((gi >> 1) & 1), err, tmo);
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) break;
+        tc::fence_after();
+        const bool gfirst_of_tile = mc < kGGroup;
+        for (int k0 = 0; k0 < KN; k0 += 16) {
+          float v[16];
+          tc::tmem_ld<16>(tmem + lane_base + accum(x, half) + (uint32_t)k0, v);
+#pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            float* q = gsum + (size_t)(k0 + u) * 256 + jl;
+            *q = gfirst_of_tile ? v[u] : *q + v[u];
+          }
+        }
+        tc::fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bars + G_ACCEMPTY + x);
+        if (mc == a.mchunks - 1) {
+          const int64_t j = tile * a.nt + jl;
+          if (jl < a.nt && j < a.N) {
+            float* gj = a.g + (size_t)j * a.K;
+            for (int k = 0; k < a.K; ++k) gj[k] = gsum[(size_t)k * 256 + jl];
+          }
+        }
+      }
+    }
+  }
+
+  // Drain: every issued MMA completes before tensor memory is freed.
+  __syncthreads();
+  if (warp == 1 && lane == 0 && shared_flags[0] > 0) {
+    tc::mma_commit(bars + G_DRAIN);
+    mbar_wait_bounded(bars + G_DRAIN, 0u, err, tmo);
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  if (warp == 1) tc::tmem_dealloc(tmem, kTmemCols);
+}
+
+// --------------------------------------------------------------- solve_c
+struct SArgs {
+  const float* g;       // [N][K]
+  float* C;             // K x N row-major
+  const float* YY;      // 2K x 2K column-major (Y^T Y, Y = [D | B])
+  __nv_bfloat16* Zt;    // [utiles][3][nu x Z16] tiles of [C_old; dl]
+  __nv_bfloat16* Ct;    // [utiles][3][KN x nu] tiles of C'^T
+  double* Vp;           // [grid][npairs] partials of V = C' C'^T (upper triangle)
+  unsigned long long* degen;
+  int K, KN, Z16, nu, reps, npairs;
+  int64_t N;
+};
 
 // Per column: reps passes of the K successive c updates, from g = B^T E and
 // G = B^T B.  With dl the change of the column so far (all repeats),
 //   t_i = g_ij - sum_l G_il dl_l ;  c_ij := [c_ij + t_i / G_ii]_+
 // (in the first pass dl_l = 0 for l >= i, so the sum runs over l < i).
-// Z (2K x N, column-major, ld 2K) receives [C_old; dl].
-__global__ void __launch_bounds__(kSolveThreads) solve_c_kernel(const float* __restrict__ g, float* C,
-                                                                const float* __restrict__ YY, float* Z,
-                                                                unsigned long long* degen, int K, int64_t N,
-                                                                int reps) {
-  extern __shared__ float Gs[];          // K x K, G_il at Gs[i*K + l]
+__global__ void __launch_bounds__(kSolveThreads) solve_c_kernel(SArgs a) {
+  extern __shared__ float shs[];
+  const int K = a.K;
+  float* Gs = shs;                       // K x K, G_il at Gs[i*K + l]
+  float* Hs = Gs + K * K;                // K x K, (B^T D)_il at Hs[i*K + l]
+  float* Cs = Hs + K * K;                // [128][K + 1] updated columns of the chunk
+  unsigned short* pairs = reinterpret_cast<unsigned short*>(Cs + kSolveThreads * (K + 1));
   const int K2 = 2 * K;
   for (int idx = threadIdx.x; idx < K * K; idx += blockDim.x) {
     const int i = idx / K, l = idx % K;
-    Gs[idx] = YY[(size_t)(K + i) + (size_t)(K + l) * K2];   // (B^T B)_il from Y^T Y
+    Gs[idx] = a.YY[(size_t)(K + i) + (size_t)(K + l) * K2];
+    Hs[idx] = a.YY[(size_t)(K + i) + (size_t)l * K2];
+  }
+  for (int e = threadIdx.x; e < a.npairs; e += blockDim.x) {
+    int i = 0, r = e;
+    while (r >= K - i) { r -= K - i; ++i; }
+    pairs[e] = (unsigned short)((i << 8) | (i + r));
   }
   __syncthreads();
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= N) return;
-  float c0[kMaxK], cur[kMaxK], dl[kMaxK];
-  const float* gj = g + (size_t)j * K;
-  for (int i = 0; i < K; ++i) {
-    c0[i] = cur[i] = C[(size_t)i * N + j];
-    dl[i] = 0.f;
-  }
-  for (int r = 0; r < reps; ++r) {
-    for (int i = 0; i < K; ++i) {
-      const int lend = r == 0 ? i : K;
-      float sl = 0.f;
-      for (int l = 0; l < lend; ++l) sl = fmaf(Gs[i * K + l], dl[l], sl);
-      const float gii = Gs[i * K + i];
-      if (gii > 0.f) {
-        const float t = cur[i] + (gj[i] - sl) / gii;
-        cur[i] = t > 0.f ? t : 0.f;
-        dl[i] = cur[i] - c0[i];
-      } else if (j == 0) {
-        atomicAdd(degen, 1ull);
+  constexpr int kPairsPerThread = (kMaxK * (kMaxK + 1) / 2 + kSolveThreads - 1) / kSolveThreads;
+  double vacc[kPairsPerThread];
+#pragma unroll
+  for (int u = 0; u < kPairsPerThread; ++u) vacc[u] = 0.0;
+
+  for (int64_t j0 = (int64_t)blockIdx.x * kSolveThreads; j0 < a.N; j0 += (int64_t)gridDim.x * kSolveThreads) {
+    const int64_t j = j0 + threadIdx.x;
+    const bool valid = j < a.N;
+    float c0[kMaxK], cur[kMaxK], dl[kMaxK], t[kMaxK];
+    if (valid) {
+      const float* gj = a.g + (size_t)j * K;
+      for (int i = 0; i < K; ++i) {
+        c0[i] = cur[i] = a.C[(size_t)i * a.N + j];
+        dl[i] = 0.f;
+      }
+      // g_j - (B^T D) c_j: the pending correction of the stored residual
+      for (int i = 0; i < K; ++i) {
+        float s = gj[i];
+        for (int l = 0; l < K; ++l) s = fmaf(-Hs[i * K + l], c0[l], s);
+        t[i] = s;
+      }
+      for (int r = 0; r < a.reps; ++r) {
+        for (int i = 0; i < K; ++i) {
+          const int lend = r == 0 ? i : K;
+          float sl = 0.f;
+          for (int l = 0; l < lend; ++l) sl = fmaf(Gs[i * K + l], dl[l], sl);
+          const float gii = Gs[i * K + i];
+          if (gii > 0.f) {
+            const float v = cur[i] + (t[i] - sl) / gii;
+            cur[i] = v > 0.f ? v : 0.f;
+            dl[i] = cur[i] - c0[i];
+          } else if (j == 0) {
+            atomicAdd(a.degen, 1ull);
+          }
+        }
+      }
+      for (int i = 0; i < K; ++i) a.C[(size_t)i * a.N + j] = cur[i];
+      // operand tiles of the update pass (three bfloat16 terms each)
+      const int64_t tile = j / a.nu;
+      const int cl = (int)(j % a.nu);
+      __nv_bfloat16* zb = a.Zt + (size_t)tile * 3 * a.nu * a.Z16;
+      const size_t zpart = (size_t)a.nu * a.Z16;
+      for (int kk = 0; kk < a.Z16; ++kk) {
+        const float v = kk < K ? c0[kk] : (kk < K2 ? dl[kk - K] : 0.f);
+        __nv_bfloat16 p0, p1, p2;
+        tc::split_bf16x3(v, p0, p1, p2);
+        const size_t o = tiled2(cl, kk, a.Z16);
+        zb[o] = p0;
+        zb[zpart + o] = p1;
+        zb[2 * zpart + o] = p2;
+      }
+      __nv_bfloat16* cb = a.Ct + (size_t)tile * 3 * a.KN * a.nu;
+      const size_t cpart = (size_t)a.KN * a.nu;
+      for (int k = 0; k < a.KN; ++k) {
+        const float v = k < K ? cur[k] : 0.f;
+        __nv_bfloat16 p0, p1, p2;
+        tc::split_bf16x3(v, p0, p1, p2);
+        const size_t o = tiled2(k, cl, a.nu);
+        cb[o] = p0;
+        cb[cpart + o] = p1;
+        cb[2 * cpart + o] = p2;
       }
     }
+    for (int i = 0; i < K; ++i) Cs[threadIdx.x * (K + 1) + i] = valid ? cur[i] : 0.f;
+    __syncthreads();
+    // V partials: this thread's pairs over the chunk's 128 columns (float32
+    // within the chunk, float64 across chunks)
+#pragma unroll
+    for (int u = 0; u < kPairsPerThread; ++u) {
+      const int e = threadIdx.x + u * kSolveThreads;
+      if (e < a.npairs) {
+        const int i = pairs[e] >> 8, l = pairs[e] & 255;
+        float s = 0.f;
+        for (int col = 0; col < kSolveThreads; ++col) s = fmaf(Cs[col * (K + 1) + i], Cs[col * (K + 1) + l], s);
+        vacc[u] += (double)s;
+      }
+    }
+    __syncthreads();
   }
-  for (int i = 0; i < K; ++i) {
-    C[(size_t)i * N + j] = cur[i];
-    Z[(size_t)i + (size_t)j * K2] = c0[i];
-    Z[(size_t)(K + i) + (size_t)j * K2] = dl[i];
+#pragma unroll
+  for (int u = 0; u < kPairsPerThread; ++u) {
+    const int e = threadIdx.x + u * kSolveThreads;
+    if (e < a.npairs) a.Vp[(size_t)blockIdx.x * a.npairs + e] = vacc[u];
   }
 }
 
-// Per row m: reps passes of the K successive b updates from W = E' C'^T and
-// V = C' C'^T (the delta-b rule of Section 4.2, over all repeats):
+size_t solve_smem(int K) {
+  return (size_t)2 * K * K * 4 + (size_t)kSolveThreads * (K + 1) * 4 + (size_t)(K * (K + 1) / 2) * 2 + 16;
+}
+
+// V (K x K, symmetric, float32) from the solve blocks' partials, added in block order.
+__global__ void vreduce_kernel(const double* Vp, int nblocks, int npairs, int K, float* V) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= npairs) return;
+  int i = 0, r = e;
+  while (r >= K - i) { r -= K - i; ++i; }
+  const int l = i + r;
+  double s = 0.0;
+  for (int b = 0; b < nblocks; ++b) s += Vp[(size_t)b * npairs + e];
+  V[(size_t)i + (size_t)l * K] = (float)s;
+  V[(size_t)l + (size_t)i * K] = (float)s;
+}
+
+// -------------------------------------------------------------- update pass
+struct UArgs {
+  const float* Y;      // ld x 2K column-major: [D | B]
+  const __nv_bfloat16* Zt;   // [utiles][3][nu x Z16]
+  const __nv_bfloat16* Ct;   // [utiles][3][KN x nu]
+  float* Wp;           // [units][KN][128] partial rows of W = E' C'^T
+  double* part_n;      // [grid] partial ||E'||^2
+  int* err;
+  int ld, K, KN, Z16, nu, RB, Q, units, stages;
+  int64_t N, utiles;
+  size_t ustage;
+  uint64_t timeout_ns;
+};
+
+enum { U_FULL = 0, U_EMPTY = 4, U_ACCFULL = 8, U_ACCEMPTY = 10, U_EREADY = 12, U_EFREE = 14, U_YREADY = 16,
+       U_WFULL = 17, U_WEMPTY = 18, U_DRAIN = 19, U_NBARS = 20 };
+
+// Tiles of one W accumulation group: the tensor cores sum a group's
+// contributions to the unit's W rows in TMEM, and the epilogue warps add the
+// group totals in float32 (round to nearest) in shared memory, which keeps
+// the accumulator chains short over the unit's many columns.
+constexpr int kWGroup = 8;
+
+__device__ __forceinline__ void unit_tiles(const UArgs& a, int u, int& rb, int64_t& t0, int64_t& t1) {
+  rb = u % a.RB;
+  const int q = u / a.RB;
+  t0 = (int64_t)q * a.utiles / a.Q;
+  t1 = (int64_t)(q + 1) * a.utiles / a.Q;
+}
+
+template <int NU>
+__global__ void __launch_bounds__(kTcThreads, 1) update_kernel(UArgs a, const __grid_constant__ CUtensorMap tmR) {
+  extern __shared__ unsigned char sm_raw[];
+  unsigned char* sm = align1024(sm_raw);
+  float* wsum = reinterpret_cast<float*>(sm + (size_t)a.stages * a.ustage);   // [KN][128] the unit's W rows
+  uint64_t* bars = reinterpret_cast<uint64_t*>(wsum + (size_t)a.KN * 128);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + U_NBARS);
+  int* shared_flags = reinterpret_cast<int*>(tmem_slot + 4);   // [0] MMA issued anything
+  double* red = reinterpret_cast<double*>(shared_flags + 4);   // [8]
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int nu = NU;
+  const int KN = a.KN, Z16 = a.Z16, S = a.stages;
+  const size_t rbytes = (size_t)nu * 128 * 4;
+  const size_t zpart = (size_t)nu * Z16 * 2;      // bytes of one term of the Z tile
+  const size_t cpart = (size_t)KN * nu * 2;       // bytes of one term of the C'^T tile
+  const size_t zbytes = 3 * zpart, cbytes = 3 * cpart;
+  // TMEM columns: two accumulators, two E' buffers (three terms of nu/2
+  // columns each), the unit's W rows, and the three terms of the Y row block.
+  const uint32_t WACC = 5 * nu, Y0 = 5 * nu + KN;
+  auto ACC = [&](int x) { return (uint32_t)(x * nu); };
+  auto EP = [&](int x, int p) { return (uint32_t)(2 * nu + x * (3 * nu / 2) + p * (nu / 2)); };
+  auto YP = [&](int p) { return Y0 + (uint32_t)(p * (Z16 / 2)); };
+
+  if (threadIdx.x == 0) {
+    shared_flags[0] = 0;
+    shared_flags[1] = 0;
+    for (int i = 0; i < U_NBARS; ++i) {
+      uint32_t cnt = 1;
+      if (i >= U_EMPTY && i < U_EMPTY + 4) cnt = 2;                      // W commit + store read
+      if (i == U_ACCEMPTY || i == U_ACCEMPTY + 1 || i == U_EREADY || i == U_EREADY + 1 || i == U_YREADY ||
+          i == U_WEMPTY)
+        cnt = kWorkWarps;
+      mbar_init(bars + i, cnt);
+    }
+  }
+  fence_mbar_init();
+  if (warp == 1) tc::tmem_alloc(tmem_slot, kTmemCols);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = *tmem_slot;
+  int* err = a.err;
+  const uint64_t tmo = a.timeout_ns;
+  const int nunits_cta = a.units > (int)blockIdx.x ? (a.units - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      int64_t i = 0;
+      bool ok = true;
+      for (int ui = 0; ui < nunits_cta && ok; ++ui) {
+        int rb;
+        int64_t t0, t1;
+        unit_tiles(a, (int)blockIdx.x + ui * (int)gridDim.x, rb, t0, t1);
+        for (int64_t t = t0; t < t1; ++t, ++i) {
+          const int s = (int)(i % S);
+          if (i >= S && !tc::wait(bars + U_EMPTY + s, (uint32_t)(((i / S) - 1) & 1), err, tmo)) {
+            ok = false;
+            break;
+          }
+          unsigned char* st = sm + (size_t)s * a.ustage;
+          mbar_arrive_expect_tx(bars + U_FULL + s, (uint32_t)(rbytes + zbytes + cbytes));
+          tc::tma_load_2d(st, &tmR, rb * 128, (int)(t * nu), bars + U_FULL + s);
+          bulk_load(st + rbytes, a.Zt + (size_t)t * 3 * nu * Z16, (uint32_t)zbytes, bars + U_FULL + s);
+          bulk_load(st + rbytes + zbytes, a.Ct + (size_t)t * 3 * KN * nu, (uint32_t)cbytes, bars + U_FULL + s);
+        }
+      }
+      for (int64_t d = std::max<int64_t>(0, i - S); d < i; ++d)
+        mbar_wait_bounded(bars + U_FULL + (d % S), (uint32_t)((d / S) & 1), err, tmo);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------- MMA issue
+    if (lane == 0) {
+      const uint32_t iU = tc::instr_desc_bf16(128, nu), iW = tc::instr_desc_bf16(128, KN);
+      int64_t i = 0;
+      bool ok = true;
+      int64_t wg = 0;     // W groups issued so far
+      // W(i): E'(i) (three terms, TMEM) times C'^T(i) (three terms, shared)
+      // into the W accumulator; rel is the tile's place in its unit of n tiles.
+      auto issue_w = [&](int64_t iw, int64_t rel, int64_t n) -> bool {
+        const int s = (int)(iw % S), x = (int)(iw & 1);
+        const bool gfirst = rel % kWGroup == 0;
+        const bool glast = rel % kWGroup == kWGroup - 1 || rel == n - 1;
+        if (!tc::wait(bars + U_EREADY + x, (uint32_t)((iw >> 1) & 1), err, tmo)) return false;
+        if (gfirst && wg > 0 && !tc::wait(bars + U_WEMPTY, (uint32_t)((wg - 1) & 1), err, tmo)) return false;
+        tc::fence_after();
+        const uint32_t sC = smem_u32(sm + (size_t)s * a.ustage + rbytes + zbytes);
+        for (int pr = 0; pr < kProds; ++pr) {
+          const uint32_t acol = EP(x, kProdA[pr]);
+          const uint32_t boff = (uint32_t)(kProdB[pr] * cpart);
+          for (int kk = 0; kk < nu / 16; ++kk) {
+            const uint64_t bd = tc::smem_desc(sC + boff + (uint32_t)kk * 256u, 128u, (uint32_t)nu * 16u);
+            tc::mma_bf16_tmem_a(tmem + WACC, tmem + acol + (uint32_t)kk * 8u, bd, iW,
+                                (gfirst && pr == 0 && kk == 0) ? 0u : 1u);
+          }
+        }
+        tc::mma_commit(bars + U_EFREE + x);
+        tc::mma_commit(bars + U_EMPTY + s);
+        if (glast) {
+          tc::mma_commit(bars + U_WFULL);
+          ++wg;
+        }
+        return true;
+      };
+      for (int ui = 0; ui < nunits_cta && ok; ++ui) {
+        int rb;
+        int64_t t0, t1;
+        unit_tiles(a, (int)blockIdx.x + ui * (int)gridDim.x, rb, t0, t1);
+        if (!tc::wait(bars + U_YREADY, (uint32_t)(ui & 1), err, tmo)) break;
+        const int64_t ifirst = i, n = t1 - t0;
+        for (int64_t t = t0; t < t1; ++t, ++i) {
+          const int s = (int)(i % S), x = (int)(i & 1);
+          if (!tc::wait(bars + U_FULL + s, (uint32_t)((i / S) & 1), err, tmo)) { ok = false; break; }
+          if (i >= 2 && !tc::wait(bars + U_ACCEMPTY + x, (uint32_t)(((i >> 1) - 1) & 1), err, tmo)) {
+            ok = false;
+            break;
+          }
+          tc::fence_after();
+          const uint32_t sZ = smem_u32(sm + (size_t)s * a.ustage + rbytes);
+          for (int pr = 0; pr < kProds; ++pr) {
+            const uint32_t acol = YP(kProdA[pr]);
+            const uint32_t boff = (uint32_t)(kProdB[pr] * zpart);
+            for (int kk = 0; kk < Z16 / 16; ++kk) {
+              const uint64_t bd = tc::smem_desc(sZ + boff + (uint32_t)kk * 256u, 128u, (uint32_t)Z16 * 16u);
+              tc::mma_bf16_tmem_a(tmem + ACC(x), tmem + acol + (uint32_t)kk * 8u, bd, iU,
+                                  (pr > 0 || kk > 0) ? 1u : 0u);
+            }
+          }
+          tc::mma_commit(bars + U_ACCFULL + x);
+          shared_flags[0] = 1;
+          if (i > ifirst && !issue_w(i - 1, i - 1 - ifirst, n)) { ok = false; break; }
+        }
+        if (!ok) break;
+        if (i > ifirst && !issue_w(i - 1, i - 1 - ifirst, n)) break;
+      }
+    }
+  } else if (warp >= 4) {
+    // --------------------------------------------------------------- epilogue
+    const int ew = warp - 4;
+    const int quarter = warp & 3, h = ew >> 2;
+    const int row = quarter * 32 + lane;
+    const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+    constexpr int hc = nu / 2;                   // columns of this warp's half of a tile
+    double acc2 = 0.0;
+    bool ok = true;
+    int64_t wgE = 0;    // W groups drained so far
+    // The epilogue warps leave their loops together: a warp that saw a wait
+    // run out raises the shared flag before the first named barrier, every
+    // warp reads it between the two (no warp writes it in between), so all
+    // take the same branch and none is left waiting at a named barrier.
+    auto collective_ok = [&](bool good) -> bool {
+      if (!good && lane == 0) *reinterpret_cast<volatile int*>(&shared_flags[1]) = 1;
+      named_bar(1, kWorkWarps * 32);
+      const int f = *reinterpret_cast<volatile int*>(&shared_flags[1]);
+      named_bar(2, kWorkWarps * 32);
+      return f == 0;
+    };
+    // Y rows of a row block into TMEM: half 0 stores terms 0 and 1, half 1 term 2.
+    auto load_y = [&](int rb) {
+      const int m = rb * 128 + row;
+      for (int k0 = 0; k0 < Z16; k0 += 16) {
+        uint32_t w0[8], w1[8], w2[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int kk = k0 + 2 * u;
+          const float y0 = (m < a.ld && kk < 2 * a.K) ? a.Y[(size_t)m + (size_t)kk * a.ld] : 0.f;
+          const float y1 = (m < a.ld && kk + 1 < 2 * a.K) ? a.Y[(size_t)m + (size_t)(kk + 1) * a.ld] : 0.f;
+          split_pair(y0, y1, w0[u], w1[u], w2[u]);
+        }
+        const uint32_t c = (uint32_t)(k0 / 2);
+        if (h == 0) {
+          tc::tmem_st_u8(tmem + lane_base + YP(0) + c, w0);
+          tc::tmem_st_u8(tmem + lane_base + YP(1) + c, w1);
+        } else {
+          tc::tmem_st_u8(tmem + lane_base + YP(2) + c, w2);
+        }
+      }
+      tc::tmem_st_wait();
+      tc::fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bars + U_YREADY);
+    };
+    int64_t i = 0;
+    if (nunits_cta > 0) {
+      int rb;
+      int64_t t0, t1;
+      unit_tiles(a, (int)blockIdx.x, rb, t0, t1);
+      load_y(rb);
+    }
+    for (int ui = 0; ui < nunits_cta && ok; ++ui) {
+      const int u = (int)blockIdx.x + ui * (int)gridDim.x;
+      int rb;
+      int64_t t0, t1;
+      unit_tiles(a, u, rb, t0, t1);
+      for (int64_t t = t0; t < t1; ++t, ++i) {
+        const int s = (int)(i % S), x = (int)(i & 1);
+        bool good = tc::wait(bars + U_ACCFULL + x, (uint32_t)((i >> 1) & 1), err, tmo) &&
+                    tc::wait(bars + U_FULL + s, (uint32_t)((i / S) & 1), err, tmo);
+        good = __all_sync(0xffffffffu, good);
+        if (good) {
+          tc::fence_after();
+          float d[hc];
+#pragma unroll
+          for (int c = 0; c < hc; c += 16)
+            tc::tmem_ld<16>(tmem + lane_base + ACC(x) + (uint32_t)(h * hc + c), d + c);
+          tc::fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(bars + U_ACCEMPTY + x);
+          // E' = R_s - Y Z on this thread's row and half of the tile; written
+          // back in place for the store, squared into the norm.
+          float* rt = reinterpret_cast<float*>(sm + (size_t)s * a.ustage) + (size_t)(h * hc) * 128 + row;
+          uint32_t e0[hc / 2], e1[hc / 2], e2[hc / 2];
+          float s2 = 0.f;
+#pragma unroll
+          for (int c = 0; c < hc; c += 2) {
+            const float ea = rt[(size_t)c * 128] - d[c];
+            const float eb = rt[(size_t)(c + 1) * 128] - d[c + 1];
+            rt[(size_t)c * 128] = ea;
+            rt[(size_t)(c + 1) * 128] = eb;
+            s2 = fmaf(ea, ea, s2);
+            s2 = fmaf(eb, eb, s2);
+            split_pair(ea, eb, e0[c / 2], e1[c / 2], e2[c / 2]);
+          }
+          acc2 += (double)s2;
+          if (i >= 2) good = tc::wait(bars + U_EFREE + x, (uint32_t)(((i >> 1) - 1) & 1), err, tmo);
+          good = __all_sync(0xffffffffu, good);
+          if (good) {
+            tc::fence_after();
+            const uint32_t c0 = (uint32_t)(h * hc / 2);
+            if (hc / 2 == 16) {
+              tc::tmem_st_u16(tmem + lane_base + EP(x, 0) + c0, e0);
+              tc::tmem_st_u16(tmem + lane_base + EP(x, 1) + c0, e1);
+              tc::tmem_st_u16(tmem + lane_base + EP(x, 2) + c0, e2);
+            } else {
+              tc::tmem_st_u8(tmem + lane_base + EP(x, 0) + c0, e0);
+              tc::tmem_st_u8(tmem + lane_base + EP(x, 1) + c0, e1);
+              tc::tmem_st_u8(tmem + lane_base + EP(x, 2) + c0, e2);
+            }
+            tc::tmem_st_wait();
+            tc::fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bars + U_EREADY + x);
+          }
+        }
+        // the tile of E' goes back to R_s by one tensor store
+        fence_proxy_async_shared();
+        if (!collective_ok(good)) {
+          ok = false;
+          break;
+        }
+        if (ew == 0 && lane == 0) {
+          tc::tma_store_2d(&tmR, rb * 128, (int)(t * nu), sm + (size_t)s * a.ustage);
+          tc::bulk_wait_read_all();
+          mbar_arrive(bars + U_EMPTY + s);
+        }
+        const int64_t rel = t - t0;
+        if (rel % kWGroup == kWGroup - 1 || t == t1 - 1) {
+          // the W group's total into the unit's rows (its first group starts them)
+          bool wgood = tc::wait(bars + U_WFULL, (uint32_t)(wgE & 1), err, tmo);
+          wgood = __all_sync(0xffffffffu, wgood);
+          if (!collective_ok(wgood)) {
+            ok = false;
+            break;
+          }
+          ++wgE;
+          tc::fence_after();
+          const int kh = KN / 2;
+          for (int k0 = 0; k0 < kh; k0 += 8) {
+            float w[8];
+            tc::tmem_ld<8>(tmem + lane_base + WACC + (uint32_t)(h * kh + k0), w);
+#pragma unroll
+            for (int v = 0; v < 8; ++v) {
+              float* q = wsum + (size_t)(h * kh + k0 + v) * 128 + row;
+              *q = rel < kWGroup ? w[v] : *q + w[v];
+            }
+          }
+          tc::fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(bars + U_WEMPTY);
+        }
+      }
+      if (!ok) break;
+      // the unit's W rows: [u][k][128]
+      for (int k = h * (KN / 2); k < (h + 1) * (KN / 2); ++k)
+        a.Wp[((size_t)u * KN + (size_t)k) * 128 + row] = wsum[(size_t)k * 128 + row];
+      if (ui + 1 < nunits_cta) {
+        int rb2;
+        int64_t s0, s1;
+        unit_tiles(a, u + (int)gridDim.x, rb2, s0, s1);
+        load_y(rb2);
+      }
+    }
+    if (ew == 0 && lane == 0) tc::bulk_wait_all();
+    acc2 = warp_sum_f64(acc2);
+    if (lane == 0) red[ew] = acc2;
+  }
+
+  __syncthreads();
+  if (warp == 1 && lane == 0 && shared_flags[0] != 0) {
+    tc::mma_commit(bars + U_DRAIN);
+    mbar_wait_bounded(bars + U_DRAIN, 0u, err, tmo);
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  if (warp == 1) tc::tmem_dealloc(tmem, kTmemCols);
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kWorkWarps; ++w) t += red[w];
+    a.part_n[blockIdx.x] = t;
+  }
+}
+
+// ---------------------------------------------------------------- B step
+// Per row m: W[m, :] = sum over the row block's column ranges (in order) of
+// the update pass's partial rows, then reps passes of the K successive b
+// updates with V = C' C'^T (the delta-b rule of Section 4.2, over all repeats):
 //   b_i := [b_i + (w_i - sum_k V_ik db_k) / V_ii]_+ ,  db = b - b_old.
 // Y (ld x 2K, column-major) holds [D | B]; B is replaced by B', D by db.
 // Block partials of sum_i db_i[m] W[m,i] in float64.
-__global__ void __launch_bounds__(kBThreads) update_b_kernel(const float* __restrict__ W, const float* __restrict__ V,
-                                                             float* Y, double* part, unsigned long long* degen,
-                                                             int K, int ld, int reps) {
-  extern __shared__ float Vs[];          // K x K, V_ik at Vs[i*K + k] (column-major V is symmetric)
+__global__ void __launch_bounds__(kBThreads) update_b_kernel(const float* __restrict__ Wp, const float* __restrict__ V,
+                                                             float* Y, double* part, unsigned long long* degen, int K,
+                                                             int KN, int ld, int RB, int Q, int reps) {
+  extern __shared__ float Vs[];          // K x K, V_ik at Vs[i*K + k] (V is symmetric)
   for (int idx = threadIdx.x; idx < K * K; idx += blockDim.x) Vs[idx] = V[idx];
   __syncthreads();
   __shared__ double red[kBThreads / 32];
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   double dw = 0.0;
   if (m < ld) {
-    float b0[kMaxK], cur[kMaxK], db[kMaxK];
+    const int rb = m >> 7, r = m & 127;
+    float w[kMaxK], b0[kMaxK], cur[kMaxK], db[kMaxK];
     for (int i = 0; i < K; ++i) {
+      double s = 0.0;
+      for (int q = 0; q < Q; ++q) s += (double)Wp[((size_t)(q * RB + rb) * KN + i) * 128 + r];
+      w[i] = (float)s;
       b0[i] = cur[i] = Y[(size_t)m + (size_t)(K + i) * ld];
       db[i] = 0.f;
     }
-    for (int r = 0; r < reps; ++r) {
+    for (int rr = 0; rr < reps; ++rr) {
       for (int i = 0; i < K; ++i) {
-        const int kend = r == 0 ? i : K;
+        const int kend = rr == 0 ? i : K;
         float s = 0.f;
         for (int k = 0; k < kend; ++k) s = fmaf(Vs[i * K + k], db[k], s);
         const float vii = Vs[i * K + i];
         if (vii > 0.f) {
-          const float t = cur[i] + (W[(size_t)m + (size_t)i * ld] - s) / vii;
+          const float t = cur[i] + (w[i] - s) / vii;
           cur[i] = t > 0.f ? t : 0.f;
           db[i] = cur[i] - b0[i];
         } else if (m == 0) {
@@ -128,50 +946,51 @@ __global__ void __launch_bounds__(kBThreads) update_b_kernel(const float* __rest
     for (int i = 0; i < K; ++i) {
       Y[(size_t)m + (size_t)(K + i) * ld] = cur[i];
       Y[(size_t)m + (size_t)i * ld] = db[i];
-      dw += (double)db[i] * (double)W[(size_t)m + (size_t)i * ld];
+      dw += (double)db[i] * (double)w[i];
     }
   }
   dw = warp_sum_f64(dw);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) red[w] = dw;
+  const int wi = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) red[wi] = dw;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double a = 0.0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) a += red[i];
-    part[blockIdx.x] = a;
+    double s = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+    part[blockIdx.x] = s;
   }
 }
 
-constexpr int kNormThreads = 256;
-
-// Per-block sums of squares of n floats (float4 loads; float32 per thread
-// within a block-stride chunk, float64 across chunks and threads).
-__global__ void __launch_bounds__(kNormThreads) norm2_kernel(const float4* __restrict__ x, int64_t n4, double* part) {
-  __shared__ double red[kNormThreads / 32];
-  double acc = 0.0;
-  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n4; i0 += (int64_t)gridDim.x * blockDim.x * 8) {
-    float s = 0.f;
+// YY = Y^T Y (2K x 2K column-major) over the ld rows of Y = [D | B]: block
+// (a, b0) forms entries (a, b0..b0+15); float32 within a thread's rows,
+// float64 across threads in a fixed tree.
+constexpr int kYYThreads = 256;
+__global__ void __launch_bounds__(kYYThreads) yy_kernel(const float* __restrict__ Y, int ld, int K2, float* YY) {
+  __shared__ double red[kYYThreads / 32][16];
+  const int a = blockIdx.x, b0 = blockIdx.y * 16;
+  float s[16];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int64_t i = i0 + threadIdx.x + (int64_t)u * gridDim.x * blockDim.x;
-      if (i < n4) {
-        const float4 v = __ldcs(x + i);
-        s = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, s))));
-      }
-    }
-    acc += (double)s;
+  for (int q = 0; q < 16; ++q) s[q] = 0.f;
+  for (int m = threadIdx.x; m < ld; m += kYYThreads) {
+    const float ya = Y[(size_t)m + (size_t)a * ld];
+#pragma unroll
+    for (int q = 0; q < 16; ++q)
+      if (b0 + q < K2) s[q] = fmaf(ya, Y[(size_t)m + (size_t)(b0 + q) * ld], s[q]);
   }
-  acc = warp_sum_f64(acc);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const double v = warp_sum_f64((double)s[q]);
+    if (l == 0) red[w][q] = v;
+  }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = 0.0;
-    for (int i = 0; i < kNormThreads / 32; ++i) a += red[i];
-    part[blockIdx.x] = a;
+  if (threadIdx.x < 16 && b0 + (int)threadIdx.x < K2) {
+    double t = 0.0;
+    for (int i = 0; i < kYYThreads / 32; ++i) t += red[i][threadIdx.x];
+    YY[(size_t)a + (size_t)(b0 + threadIdx.x) * K2] = (float)t;
   }
 }
 
-// f after the sweep: ||E'||^2 from the norm pass, then the B step identity.
+// f after the sweep: ||E'||^2 from the update pass, then the B step identity.
 __global__ void objective_kernel(const double* part_n, int nn, const double* part_b, int nb, const float* YY,
                                  const float* V, int K, double* state, double* trace_out) {
   __shared__ double red[8];
@@ -196,81 +1015,129 @@ __global__ void objective_kernel(const double* part_n, int nn, const double* par
   }
 }
 
+// R_s := R_s - D C (the pending correction applied): a thread per row holds
+// that row of D in registers and walks the block's columns.
+constexpr int kMatThreads = 128;
+__global__ void __launch_bounds__(kMatThreads) apply_pending_kernel(float* R, const float* __restrict__ Y,
+                                                                    const float* __restrict__ C, int ld, int64_t N,
+                                                                    int K, int cols_per_block) {
+  __shared__ float cs[kMaxK];
+  const int64_t j0 = (int64_t)blockIdx.y * cols_per_block;
+  const int64_t j1 = std::min<int64_t>(N, j0 + cols_per_block);
+  const int m = blockIdx.x * kMatThreads + threadIdx.x;
+  float d[kMaxK];
+#pragma unroll
+  for (int k = 0; k < kMaxK; ++k) d[k] = (m < ld && k < K) ? Y[(size_t)m + (size_t)k * ld] : 0.f;
+  for (int64_t j = j0; j < j1; ++j) {
+    __syncthreads();
+    if (threadIdx.x < K) cs[threadIdx.x] = C[(size_t)threadIdx.x * N + j];
+    __syncthreads();
+    if (m < ld) {
+      float s = 0.f;
+#pragma unroll
+      for (int k = 0; k < kMaxK; ++k)
+        if (k < K) s = fmaf(d[k], cs[k], s);
+      R[(size_t)j * ld + m] -= s;
+    }
+  }
+}
+
 }  // namespace
 
 struct BatchedState {
-  cublasHandle_t blas = nullptr;
-  cublasComputeType_t compute = CUBLAS_COMPUTE_32F_PEDANTIC;
-  float *g = nullptr, *Z = nullptr, *W = nullptr, *V = nullptr, *YY = nullptr;
-  double *part_b = nullptr, *part_n = nullptr, *state = nullptr;
-  int nc = 0, nb = 0, nn = 0;
+  BPlan P{};
+  __nv_bfloat16 *Bg = nullptr, *Zt = nullptr, *Ct = nullptr;
+  float *g = nullptr, *Wp = nullptr, *V = nullptr, *YY = nullptr;
+  double *Vp = nullptr, *part_b = nullptr, *part_n = nullptr, *state = nullptr;
+  int* err = nullptr;
+  int nb = 0;
   bool d_pending = false;
+  const float* mapped_R = nullptr;
+  CUtensorMap tmG{}, tmU{};
 };
 
 bool batched_supported(int K) { return K >= 1 && K <= kMaxK; }
 
-// Column-major float32 GEMM C = alpha op(A) op(B) + beta C in the state's compute type.
-static bool gemm(BatchedState* b, cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k, float alpha,
-                 const float* A, int lda, const float* B, int ldb, float beta, float* C, int ldc) {
-  return cublasGemmEx(b->blas, ta, tb, m, n, k, &alpha, A, CUDA_R_32F, lda, B, CUDA_R_32F, ldb, &beta, C, CUDA_R_32F,
-                      ldc, b->compute, CUBLAS_GEMM_DEFAULT) == CUBLAS_STATUS_SUCCESS;
+static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct WsLayout {
+  size_t Bg, g, Zt, Ct, Wp, V, YY, Vp, part_b, part_n, state, err, total;
+};
+
+static WsLayout ws_layout(const BPlan& P) {
+  WsLayout L;
+  size_t o = 0;
+  L.Bg = o;     o += al((size_t)P.mchunks * 3 * P.KN * kGChunk * 2);
+  L.g = o;      o += al((size_t)P.K * P.N * 4);
+  L.Zt = o;     o += al((size_t)P.utiles * 3 * P.nu * P.Z16 * 2);
+  L.Ct = o;     o += al((size_t)P.utiles * 3 * P.KN * P.nu * 2);
+  L.Wp = o;     o += al((size_t)P.units * P.KN * 128 * 4);
+  L.V = o;      o += al((size_t)P.K * P.K * 4);
+  L.YY = o;     o += al((size_t)4 * P.K * P.K * 4);
+  L.Vp = o;     o += al((size_t)P.sgrid * P.npairs * 8);
+  L.part_b = o; o += al((size_t)((P.ld + kBThreads - 1) / kBThreads) * 8);
+  L.part_n = o; o += al((size_t)kNormPartMax * 8);
+  L.state = o;  o += al(2 * 8);
+  L.err = o;    o += al(16);
+  L.total = o;
+  return L;
 }
 
 size_t batched_workspace_bytes(int ld, int64_t N, int K) {
-  const int nb = (ld + kBThreads - 1) / kBThreads;
-  return (size_t)K * N * 4 + (size_t)2 * K * N * 4 + (size_t)ld * K * 4 + (size_t)K * K * 4 + (size_t)4 * K * K * 4 +
-         (size_t)(nb + 2 + 4096) * 8 + 8 * 256;
+  BPlan P;
+  if (!make_plan(ld, N, K, &P)) return 0;
+  return ws_layout(P).total;
 }
 
-static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
-
-BatchedState* batched_create(void* ws, int ld, int64_t N, int K, bool bf16x9, cudaStream_t s) {
+BatchedState* batched_create(void* ws, int ld, int64_t N, int K, cudaStream_t s) {
   BatchedState* b = new BatchedState();
-  if (cublasCreate(&b->blas) != CUBLAS_STATUS_SUCCESS) {
+  if (!make_plan(ld, N, K, &b->P) || b->P.ugrid > kNormPartMax) {
     delete b;
     return nullptr;
   }
-  cublasSetStream(b->blas, s);
-  if (bf16x9) {
-    // float32 emulated on the bfloat16 tensor cores, used for every shape
-    b->compute = CUBLAS_COMPUTE_32F_EMULATED_16BFX9;
-    cublasSetMathMode(b->blas, CUBLAS_FP32_EMULATED_BF16X9_MATH);
-    cublasSetEmulationStrategy(b->blas, CUBLAS_EMULATION_STRATEGY_EAGER);
-  } else {
-    b->compute = CUBLAS_COMPUTE_32F_PEDANTIC;
-    cublasSetMathMode(b->blas, CUBLAS_PEDANTIC_MATH);   // float32 products, no reduced-precision shortcuts
-  }
-  b->nc = (int)((N + kSolveThreads - 1) / kSolveThreads);
-  b->nb = (ld + kBThreads - 1) / kBThreads;
+  const WsLayout L = ws_layout(b->P);
   unsigned char* p = static_cast<unsigned char*>(ws);
-  auto take = [&](size_t n) { void* q = p; p += al(n); return q; };
-  b->g = (float*)take((size_t)K * N * 4);
-  b->Z = (float*)take((size_t)2 * K * N * 4);
-  b->W = (float*)take((size_t)ld * K * 4);
-  b->V = (float*)take((size_t)K * K * 4);
-  b->YY = (float*)take((size_t)4 * K * K * 4);
-  b->part_b = (double*)take((size_t)b->nb * 8);
-  b->part_n = (double*)take((size_t)4096 * 8);
-  b->state = (double*)take(2 * 8);
-  int dev = 0, sms = 0;
+  b->Bg = (__nv_bfloat16*)(p + L.Bg);
+  b->g = (float*)(p + L.g);
+  b->Zt = (__nv_bfloat16*)(p + L.Zt);
+  b->Ct = (__nv_bfloat16*)(p + L.Ct);
+  b->Wp = (float*)(p + L.Wp);
+  b->V = (float*)(p + L.V);
+  b->YY = (float*)(p + L.YY);
+  b->Vp = (double*)(p + L.Vp);
+  b->part_b = (double*)(p + L.part_b);
+  b->part_n = (double*)(p + L.part_n);
+  b->state = (double*)(p + L.state);
+  b->err = (int*)(p + L.err);
+  b->nb = (ld + kBThreads - 1) / kBThreads;
+  // the operand tiles past column N stay zero
+  // (the tensor-core kernels' limit is the device maximum, so contexts of
+  // different shapes never lower it under one another)
+  int dev = 0, optin = 0;
   cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  b->nn = sms * 4 < 4096 ? sms * 4 : 4096;
-  // G and V staged in shared memory: K*K floats, 64 KB at K = 128
-  const int kk = K * K * 4;
-  if (cudaFuncSetAttribute(solve_c_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kk) != cudaSuccess ||
-      cudaFuncSetAttribute(update_b_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kk) != cudaSuccess) {
-    cublasDestroy(b->blas);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (cudaMemsetAsync(ws, 0, L.total, s) != cudaSuccess || (size_t)optin < std::max(b->P.gsmem, b->P.usmem) ||
+      cudaFuncSetAttribute(g_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess ||
+      cudaFuncSetAttribute(update_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess ||
+      cudaFuncSetAttribute(update_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess ||
+      cudaFuncSetAttribute(solve_c_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)solve_smem(K)) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(update_b_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, K * K * 4) != cudaSuccess) {
+    cudaGetLastError();
     delete b;
     return nullptr;
   }
   return b;
 }
 
-void batched_destroy(BatchedState* b) {
-  if (!b) return;
-  if (b->blas) cublasDestroy(b->blas);
-  delete b;
+void batched_destroy(BatchedState* b) { delete b; }
+
+int* batched_error_word(BatchedState* b) { return b->err; }
+
+static cudaError_t launch_yy(BatchedState* b, const float* Y, int ld, int K, cudaStream_t s) {
+  const int K2 = 2 * K;
+  yy_kernel<<<dim3(K2, (K2 + 15) / 16), kYYThreads, 0, s>>>(Y, ld, K2, b->YY);
+  return cudaGetLastError();
 }
 
 // After a refresh (R_s = X - B C exactly): D = 0, Y^T Y and ||E||^2 anew.
@@ -279,68 +1146,131 @@ cudaError_t batched_reset(BatchedState* b, float* Y, int ld, int K, double e2, c
   if (e != cudaSuccess) return e;
   e = cudaMemcpyAsync(b->state, &e2, sizeof(double), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return e;
-  if (!gemm(b, CUBLAS_OP_T, CUBLAS_OP_N, 2 * K, 2 * K, ld, 1.f, Y, ld, Y, ld, 0.f, b->YY, 2 * K))
-    return cudaErrorUnknown;
+  e = launch_yy(b, Y, ld, K, s);
+  if (e != cudaSuccess) return e;
   b->d_pending = false;
   // the host value e2 must stay valid until the copy ran
   return cudaStreamSynchronize(s);
 }
 
+static bool encode_maps(BatchedState* b, const float* R) {
+  if (b->mapped_R == R) return true;
+  const BPlan& P = b->P;
+  if (!encode_f32_colmajor(&b->tmG, R, P.ld, P.N, P.ld, kGChunk, P.nt, CU_TENSOR_MAP_SWIZZLE_128B) ||
+      !encode_f32_colmajor(&b->tmU, R, P.ld, P.N, P.ld, 128, P.nu, CU_TENSOR_MAP_SWIZZLE_NONE))
+    return false;
+  b->mapped_R = R;
+  return true;
+}
+
 // One batched sweep.  R (ld x N), Y = [D | B] (ld x 2K), C (K x N row-major).
 cudaError_t batched_sweep(BatchedState* b, float* R, float* Y, float* C, int ld, int64_t N, int K, int reps_c,
-                          int reps_b, unsigned long long* degen, double* trace_out, cudaStream_t s) {
-  const int K2 = 2 * K;
+                          int reps_b, unsigned long long* degen, uint64_t timeout_ns, double* trace_out,
+                          cudaStream_t s) {
+  const BPlan& P = b->P;
+  if (!encode_maps(b, R)) return cudaErrorInvalidValue;
+  const int sms = sm_count();
   float* Bm = Y + (size_t)K * ld;
-  // g = B^T R_s  (K x N) ;  g -= (B^T D) C
-  if (!gemm(b, CUBLAS_OP_T, CUBLAS_OP_N, K, (int)N, ld, 1.f, Bm, ld, R, ld, 0.f, b->g, K))
-    return cudaErrorUnknown;
-  if (b->d_pending) {
-    // H = (B^T D) is the block rows K..2K-1, columns 0..K-1 of Y^T Y.
-    if (!gemm(b, CUBLAS_OP_N, CUBLAS_OP_T, K, (int)N, K, -1.f, b->YY + K, K2, C, (int)N, 1.f, b->g, K))
-      return cudaErrorUnknown;
-  }
-  solve_c_kernel<<<b->nc, kSolveThreads, (size_t)K * K * 4, s>>>(b->g, C, b->YY, b->Z, degen, K, N, reps_c);
+  // g = B^T R_s (the pending (B^T D) C term is taken in the solve)
+  prep_gb_kernel<<<sms * 2, 256, 0, s>>>(Bm, ld, ld, K, P.KN, P.mchunks, b->Bg);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  // R_s := R_s - [D B] [C_old; dl]  (the D half only while a correction is pending)
-  if (b->d_pending) {
-    if (!gemm(b, CUBLAS_OP_N, CUBLAS_OP_N, ld, (int)N, K2, -1.f, Y, ld, b->Z, K2, 1.f, R, ld))
-      return cudaErrorUnknown;
-  } else {
-    if (!gemm(b, CUBLAS_OP_N, CUBLAS_OP_N, ld, (int)N, K, -1.f, Bm, ld, b->Z + K, K2, 1.f, R, ld))
-      return cudaErrorUnknown;
-  }
-  // ||E'||^2 of the updated residual (ld*N is a multiple of 4: ld is)
-  norm2_kernel<<<b->nn, kNormThreads, 0, s>>>(reinterpret_cast<const float4*>(R), (int64_t)ld * N / 4, b->part_n);
+  GArgs ga{};
+  ga.Bg = b->Bg;
+  ga.g = b->g;
+  ga.err = b->err;
+  ga.ld = ld;
+  ga.K = K;
+  ga.KN = P.KN;
+  ga.nt = P.nt;
+  ga.mchunks = P.mchunks;
+  ga.N = N;
+  ga.gtiles = P.gtiles;
+  ga.gstage = P.gstage;
+  ga.timeout_ns = timeout_ns;
+  g_kernel<<<P.ggrid, kTcThreads, P.gsmem, s>>>(ga, b->tmG);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  // W = R C'^T (ld x K), V = C' C'^T (K x K): C' row-major K x N is column-major N x K.
-  if (!gemm(b, CUBLAS_OP_N, CUBLAS_OP_N, ld, K, (int)N, 1.f, R, ld, C, (int)N, 0.f, b->W, ld))
-    return cudaErrorUnknown;
-  if (!gemm(b, CUBLAS_OP_T, CUBLAS_OP_N, K, K, (int)N, 1.f, C, (int)N, C, (int)N, 0.f, b->V, K))
-    return cudaErrorUnknown;
-  update_b_kernel<<<b->nb, kBThreads, (size_t)K * K * 4, s>>>(b->W, b->V, Y, b->part_b, degen, K, ld, reps_b);
+  // the K successive c updates per column, with the next pass's operand tiles and V partials
+  SArgs sa{};
+  sa.g = b->g;
+  sa.C = C;
+  sa.YY = b->YY;
+  sa.Zt = b->Zt;
+  sa.Ct = b->Ct;
+  sa.Vp = b->Vp;
+  sa.degen = degen;
+  sa.K = K;
+  sa.KN = P.KN;
+  sa.Z16 = P.Z16;
+  sa.nu = P.nu;
+  sa.reps = reps_c;
+  sa.npairs = P.npairs;
+  sa.N = N;
+  solve_c_kernel<<<P.sgrid, kSolveThreads, solve_smem(K), s>>>(sa);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  vreduce_kernel<<<(P.npairs + 127) / 128, 128, 0, s>>>(b->Vp, P.sgrid, P.npairs, K, b->V);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // R_s := R_s - [D B] [C_old; dl], ||E'||^2, W = E' C'^T partials
+  UArgs ua{};
+  ua.Y = Y;
+  ua.Zt = b->Zt;
+  ua.Ct = b->Ct;
+  ua.Wp = b->Wp;
+  ua.part_n = b->part_n;
+  ua.err = b->err;
+  ua.ld = ld;
+  ua.K = K;
+  ua.KN = P.KN;
+  ua.Z16 = P.Z16;
+  ua.nu = P.nu;
+  ua.RB = P.RB;
+  ua.Q = P.Q;
+  ua.units = P.units;
+  ua.stages = P.ustages;
+  ua.N = N;
+  ua.utiles = P.utiles;
+  ua.ustage = P.ustage;
+  ua.timeout_ns = timeout_ns;
+  if (P.nu == 64)
+    update_kernel<64><<<P.ugrid, kTcThreads, P.usmem, s>>>(ua, b->tmU);
+  else
+    update_kernel<32><<<P.ugrid, kTcThreads, P.usmem, s>>>(ua, b->tmU);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  update_b_kernel<<<b->nb, kBThreads, (size_t)K * K * 4, s>>>(b->Wp, b->V, Y, b->part_b, degen, K, P.KN, ld, P.RB,
+                                                               P.Q, reps_b);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // Y^T Y gives B^T B, B^T D and D^T D for the objective and the next sweep.
-  if (!gemm(b, CUBLAS_OP_T, CUBLAS_OP_N, K2, K2, ld, 1.f, Y, ld, Y, ld, 0.f, b->YY, K2))
-    return cudaErrorUnknown;
-  objective_kernel<<<1, 256, 0, s>>>(b->part_n, b->nn, b->part_b, b->nb, b->YY, b->V, K, b->state, trace_out);
+  e = launch_yy(b, Y, ld, K, s);
+  if (e != cudaSuccess) return e;
+  objective_kernel<<<1, 256, 0, s>>>(b->part_n, P.ugrid, b->part_b, b->nb, b->YY, b->V, K, b->state, trace_out);
   e = cudaGetLastError();
   b->d_pending = true;
   return e;
 }
 
+int batched_launches_per_sweep() { return 8; }
+
+// Passes of R_s per sweep: the g pass reads it, the update pass reads and writes it.
+int batched_passes_per_sweep() { return 3; }
+
 // R_s := R_s - D C and D = 0: the stored residual becomes the true one.
 cudaError_t batched_materialize(BatchedState* b, float* R, float* Y, const float* C, int ld, int64_t N, int K,
                                 cudaStream_t s) {
   if (!b->d_pending) return cudaSuccess;
-  if (!gemm(b, CUBLAS_OP_N, CUBLAS_OP_T, ld, (int)N, K, -1.f, Y, ld, C, (int)N, 1.f, R, ld))
-    return cudaErrorUnknown;
-  cudaError_t e = cudaMemsetAsync(Y, 0, (size_t)ld * K * 4, s);
+  const int cols = 512;
+  const dim3 grid((ld + kMatThreads - 1) / kMatThreads, (unsigned)((N + cols - 1) / cols));
+  apply_pending_kernel<<<grid, kMatThreads, 0, s>>>(R, Y, C, ld, N, K, cols);
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if (!gemm(b, CUBLAS_OP_T, CUBLAS_OP_N, 2 * K, 2 * K, ld, 1.f, Y, ld, Y, ld, 0.f, b->YY, 2 * K))
-    return cudaErrorUnknown;
+  e = cudaMemsetAsync(Y, 0, (size_t)ld * K * 4, s);
+  if (e != cudaSuccess) return e;
+  e = launch_yy(b, Y, ld, K, s);
+  if (e != cudaSuccess) return e;
   b->d_pending = false;
   return cudaSuccess;
 }

@@ -368,15 +368,19 @@ cudaError_t launch_refresh_tc(const float* X, void* R, const float* B, const flo
                               int K, void* workspace, double* part, float* P1, double* CC1, int* err,
                               uint64_t timeout_ns, cudaStream_t s, bool f32);
 
-// Batched DID (Algorithm 3 with one reduction per sweep; cuBLAS GEMMs).
+// Batched DID (Algorithm 3 with one reduction per sweep) on the library's
+// tensor-core kernels (did_batched.cu); K <= 64.
 struct BatchedState;
 bool batched_supported(int K);
-size_t batched_workspace_bytes(int ld, int64_t N, int K);
-BatchedState* batched_create(void* ws, int ld, int64_t N, int K, bool bf16x9, cudaStream_t s);
+size_t batched_workspace_bytes(int ld, int64_t N, int K);   // 0: shape not supported
+BatchedState* batched_create(void* ws, int ld, int64_t N, int K, cudaStream_t s);
 void batched_destroy(BatchedState* b);
+int* batched_error_word(BatchedState* b);                   // device word, nonzero after a wait ran out
+int batched_launches_per_sweep();
+int batched_passes_per_sweep();
 cudaError_t batched_reset(BatchedState* b, float* Y, int ld, int K, double e2, cudaStream_t s);
 cudaError_t batched_sweep(BatchedState* b, float* R, float* Y, float* C, int ld, int64_t N, int K, int reps_c, int reps_b,
-                          unsigned long long* degen, double* trace_out, cudaStream_t s);
+                          unsigned long long* degen, uint64_t timeout_ns, double* trace_out, cudaStream_t s);
 cudaError_t batched_materialize(BatchedState* b, float* R, float* Y, const float* C, int ld, int64_t N, int K,
                                 cudaStream_t s);
 

@@ -22,8 +22,9 @@
 //               and one elected thread issues the tcgen05.mma instructions;
 //   warps 4-11  epilogue, two warps per TMEM lane quarter (warp w reads lanes
 //               32 (w % 4).. and columns 32 ((w - 4) / 4)..): tcgen05.ld of the
-//               accumulator, R = X - D (rounded to bfloat16 for that mode),
-//               stored, and the sum of R^2 accumulated in float64.  When
+//               accumulator, R = X - D (rounded to bfloat16 for that mode)
+//               written over the X tile in shared memory and stored by one
+//               2-D tensor copy, and the sum of R^2 accumulated in float64.  When
 //               asked, the epilogue also forms the partials of R c_1^T that
 //               the first b-update of the next sweep needs (one row of
 //               partials per CTA and column half, summed over the CTA's
@@ -39,12 +40,9 @@
 // Every mbarrier wait is bounded; on expiry the kernel records the error,
 // stops issuing work, waits (bounded) for its copies and MMAs, frees its
 // TMEM and returns.
-#include "did_internal.cuh"
+#include "did_tc.cuh"
 
-#include <cudaTypedefs.h>
 #include <stdio.h>
-
-#include <mutex>
 
 namespace did {
 
@@ -75,85 +73,6 @@ struct TcArgs {
   uint64_t timeout_ns;
 };
 
-// ------------------------------------------------------------- descriptors
-// Shared-memory matrix descriptor of tcgen05 (no swizzle, K-major):
-// start address >> 4 in bits 0-13, leading (K-direction) byte offset >> 4 in
-// bits 16-29, stride (M/N-direction) byte offset >> 4 in bits 32-45, the
-// descriptor version 1 in bits 46-47, base offset 0, swizzle mode 0.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-  d |= (uint64_t)1 << 46;
-  return d;
-}
-
-// Instruction descriptor of tcgen05.mma kind::f16: dense, D float32 (bits
-// 4-5 = 1), A and B bfloat16 (bits 7-9 = 1, bits 10-12 = 1), both K-major
-// (bits 15, 16 = 0), N >> 3 in bits 17-22, M >> 4 in bits 24-28.
-__host__ __device__ constexpr uint32_t instr_desc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-// kind::tf32: the same fields with A and B of format TF32 (value 2).
-__host__ __device__ constexpr uint32_t instr_desc_tf32(int M, int N) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-// -------------------------------------------------------------- tcgen05 ops
-__device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
-               "r"(ncols)
-               : "memory");
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// 16 consecutive float32 accumulator columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// Bounded wait used by every role; returns false once the error word is set.
-__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, int* err, uint64_t timeout_ns) {
-  if (ld_volatile(err) != 0) return false;
-  return mbar_wait_bounded(bar, parity, err, timeout_ns);
-}
-
 // Shared memory plan (bytes).
 struct TcSmem {
   size_t A, B, X, bars, tmem_slot, red, steps, total;
@@ -178,7 +97,7 @@ enum {
   BAR_A_FULL = 1,     // 1, 2: B-factor row block buffers landed
   BAR_A_EMPTY = 3,    // 3, 4: MMAs of a step done reading its A buffer (and B)
   BAR_X_FULL = 5,     // 5, 6: X tile buffers landed
-  BAR_X_EMPTY = 7,    // 7, 8: epilogue done with an X buffer (one arrival per epilogue warp)
+  BAR_X_EMPTY = 7,    // 7, 8: the R tile stored from an X buffer has been read out
   BAR_ACC_FULL = 9,   // 9, 10: accumulator ready (tcgen05.commit)
   BAR_ACC_EMPTY = 11, // 11, 12: epilogue done reading an accumulator (one arrival per epilogue warp)
   BAR_COUNT = 13
@@ -186,7 +105,8 @@ enum {
 
 // F32: TF32x3 operands and a float32 residual; otherwise BF16x3 and bfloat16.
 template <bool F32>
-__global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a, const __grid_constant__ CUtensorMap tmX) {
+__global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a, const __grid_constant__ CUtensorMap tmX,
+                                                                  const __grid_constant__ CUtensorMap tmR) {
   constexpr int E = F32 ? 4 : 2;                  // operand element bytes
   constexpr int KSTEP = F32 ? 8 : 16;             // K per MMA (32 bytes)
   extern __shared__ __align__(1024) unsigned char sm[];
@@ -207,17 +127,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a, con
   const uint32_t b_split = (uint32_t)kTileN * Kp * E;
 
   if (threadIdx.x == 0) {
-    *mma_steps = 0;
+    mma_steps[0] = 0;
+    mma_steps[1] = 0;     // epilogue failure flag
     for (int i = 0; i < BAR_COUNT; ++i) {
-      const bool per_warp = (i == BAR_X_EMPTY || i == BAR_X_EMPTY + 1 || i == BAR_ACC_EMPTY || i == BAR_ACC_EMPTY + 1);
+      const bool per_warp = i == BAR_ACC_EMPTY || i == BAR_ACC_EMPTY + 1;
       mbar_init(bars + i, per_warp ? kEpiWarps : 1);
     }
   }
   fence_mbar_init();
-  if (warp == 1) tmem_alloc(tmem_slot, kTmemCols);
-  tc_fence_before();
+  if (warp == 1) tc::tmem_alloc(tmem_slot, kTmemCols);
+  tc::fence_before();
   __syncthreads();
-  tc_fence_after();
+  tc::fence_after();
   const uint32_t tmem = *tmem_slot;
 
   // The CTA's work list: column tiles t = blockIdx.x + i*grid, each with all
@@ -240,7 +161,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a, con
         if (rb == 0 && s > 0) {
           // the previous tile's MMAs (all of them: commits complete in order)
           // must be done with the C-factor buffer
-          if (!tc_wait(bars + BAR_A_EMPTY + ((s - 1) & 1), (uint32_t)(((s - 1) >> 1) & 1), err, tmo)) break;
+          if (!tc::wait(bars + BAR_A_EMPTY + ((s - 1) & 1), (uint32_t)(((s - 1) >> 1) & 1), err, tmo)) break;
         }
         if (rb == 0) {
           mbar_arrive_expect_tx(bars + BAR_B_FULL, b_bytes);
@@ -248,7 +169,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a, con
                     bars + BAR_B_FULL);
         }
         const int abuf = (int)(s & 1);
-        if (s >= 2 && !tc_wait(bars + BAR_A_EMPTY + abuf, (uint32_t)(((s - 2) >> 1) & 1), err, tmo)) break;
+        if (s >= 2 && !tc::wait(bars + BAR_A_EMPTY + abuf, (uint32_t)(((s - 2) >> 1) & 1), err, tmo)) break;
         mbar_arrive_expect_tx(bars + BAR_A_FULL + abuf, a_bytes);
         bulk_load(sA + (size_t)abuf * a_bytes, reinterpret_cast<const unsigned char*>(a.Ahl) + (size_t)rb * a_bytes,
                   a_bytes, bars + BAR_A_FULL + abuf);
@@ -256,7 +177,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a, con
         // buffer s & 1 (element (row, c) at c*128 + row; rows past ld and
         // columns past N are filled with zeros and count in the bytes)
         const int xb = (int)(s & 1);
-        if (s >= 2 && !tc_wait(bars + BAR_X_EMPTY + xb, (uint32_t)(((s - 2) >> 1) & 1), err, tmo)) break;
+        if (s >= 2 && !tc::wait(bars + BAR_X_EMPTY + xb, (uint32_t)(((s - 2) >> 1) & 1), err, tmo)) break;
         mbar_arrive_expect_tx(bars + BAR_X_FULL + xb, (uint32_t)(kTileM * kTileN * 4));
         asm volatile(
             "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
@@ -268,17 +189,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a, con
   } else if (warp == 1) {
     // ----------------------------------------------------------- MMA issue
     if (lane == 0) {
-      const uint32_t idesc = F32 ? instr_desc_tf32(kTileM, kTileN) : instr_desc_bf16(kTileM, kTileN);
+      const uint32_t idesc = F32 ? tc::instr_desc_tf32(kTileM, kTileN) : tc::instr_desc_bf16(kTileM, kTileN);
       const uint32_t sA0 = smem_u32(sA), sB0 = smem_u32(sB);
       const uint32_t sbo = (uint32_t)Kp * E * 8;   // next 8-row group
       for (int64_t s = 0; s < nsteps; ++s) {
         const int rb = (int)(s % a.row_blocks);
         const int64_t ti = s / a.row_blocks;
-        if (rb == 0 && !tc_wait(bars + BAR_B_FULL, (uint32_t)(ti & 1), err, tmo)) break;
+        if (rb == 0 && !tc::wait(bars + BAR_B_FULL, (uint32_t)(ti & 1), err, tmo)) break;
         const int ab = (int)(s & 1);             // accumulator and A buffer of this step
-        if (!tc_wait(bars + BAR_A_FULL + ab, (uint32_t)((s >> 1) & 1), err, tmo)) break;
-        if (s >= 2 && !tc_wait(bars + BAR_ACC_EMPTY + ab, (uint32_t)(((s - 2) >> 1) & 1), err, tmo)) break;
-        tc_fence_after();
+        if (!tc::wait(bars + BAR_A_FULL + ab, (uint32_t)((s >> 1) & 1), err, tmo)) break;
+        if (s >= 2 && !tc::wait(bars + BAR_ACC_EMPTY + ab, (uint32_t)(((s - 2) >> 1) & 1), err, tmo)) break;
+        tc::fence_after();
         const uint32_t d = tmem + (uint32_t)(ab * kTileN);
         uint32_t acc = 0;
         // Bh Ch, Bh Cl, Bl Ch
@@ -286,17 +207,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a, con
           const uint32_t aoff = prod == 2 ? a_split : 0u;
           const uint32_t boff = prod == 1 ? b_split : 0u;
           for (int kk = 0; kk < Kp / KSTEP; ++kk) {
-            const uint64_t ad = smem_desc(sA0 + (uint32_t)ab * a_bytes + aoff + (uint32_t)kk * 256u, 128u, sbo);
-            const uint64_t bd = smem_desc(sB0 + boff + (uint32_t)kk * 256u, 128u, sbo);
+            const uint64_t ad = tc::smem_desc(sA0 + (uint32_t)ab * a_bytes + aoff + (uint32_t)kk * 256u, 128u, sbo);
+            const uint64_t bd = tc::smem_desc(sB0 + boff + (uint32_t)kk * 256u, 128u, sbo);
             if (F32)
-              mma_tf32(d, ad, bd, idesc, acc);
+              tc::mma_tf32(d, ad, bd, idesc, acc);
             else
-              mma_bf16(d, ad, bd, idesc, acc);
+              tc::mma_bf16(d, ad, bd, idesc, acc);
             acc = 1;
           }
         }
-        mma_commit(bars + BAR_ACC_FULL + ab);
-        mma_commit(bars + BAR_A_EMPTY + ab);
+        tc::mma_commit(bars + BAR_ACC_FULL + ab);
+        tc::mma_commit(bars + BAR_A_EMPTY + ab);
         *mma_steps = (int)(s + 1);
       }
     }
@@ -310,6 +231,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a, con
     float* prow = a.c1 ? a.P1 + (size_t)(2 * blockIdx.x + half) * a.ld : nullptr;
     double acc2 = 0.0, cc1 = 0.0;
     bool ok = true;
+    // A warp that saw a wait run out raises the shared flag before the first
+    // named barrier; every warp reads it between the two, so all take the
+    // same branch.
+    auto collective_ok = [&](bool good) -> bool {
+      if (!good && lane == 0) *reinterpret_cast<volatile int*>(mma_steps + 1) = 1;
+      named_bar(1, kEpiWarps * 32);
+      const int f = *reinterpret_cast<volatile int*>(mma_steps + 1);
+      named_bar(2, kEpiWarps * 32);
+      return f == 0;
+    };
     for (int64_t s = 0; s < nsteps && ok; ++s) {
       const int64_t ti = s / a.row_blocks;
       const int rb = (int)(s % a.row_blocks);
@@ -326,46 +257,27 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a, con
         if (ti > 0 && i < a.ld) pold = __ldcg(prow + i);
         if (lane < ncol) cv = __ldg(a.c1 + j0 + c0 + lane);
       }
-      ok = tc_wait(bars + BAR_ACC_FULL + ab, (uint32_t)((s >> 1) & 1), err, tmo) &&
-           tc_wait(bars + BAR_X_FULL + xb, (uint32_t)((s >> 1) & 1), err, tmo);
+      ok = tc::wait(bars + BAR_ACC_FULL + ab, (uint32_t)((s >> 1) & 1), err, tmo) &&
+           tc::wait(bars + BAR_X_FULL + xb, (uint32_t)((s >> 1) & 1), err, tmo);
       // the warp-wide tcgen05.ld below needs every lane, so the lanes agree
       ok = __all_sync(0xffffffffu, ok);
-      tc_fence_after();
+      tc::fence_after();
       float d[kTileN / 2];
 #pragma unroll
       for (int c = 0; c < kTileN / 2; c += 16)
-        tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ab * kTileN + c0 + c), d + c);
-      tc_fence_before();
+        tc::tmem_ld<16>(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ab * kTileN + c0 + c), d + c);
+      tc::fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(bars + BAR_ACC_EMPTY + ab);
-      const float* xs = sX + (size_t)xb * kTileN * kTileM + (size_t)c0 * kTileM + row_in;
+      float* xs = sX + (size_t)xb * kTileN * kTileM + (size_t)c0 * kTileM + row_in;
       float s2 = 0.f;
-      if (ok && i < a.ld) {
-        if (F32) {
-          float* rp = static_cast<float*>(a.R) + (size_t)(j0 + c0) * a.ld + i;
+      // R = X - B C for this thread's row and 32 columns, rounded to the
+      // residual's precision (values past N or ld are cut by the store).
 #pragma unroll
-          for (int c = 0; c < kTileN / 2; ++c) {
-            if (c < ncol) {
-              const float r = xs[c * kTileM] - d[c];
-              rp[(size_t)c * a.ld] = r;
-              s2 = fmaf(r, r, s2);
-              d[c] = r;
-            }
-          }
-        } else {
-          __nv_bfloat16* rp = static_cast<__nv_bfloat16*>(a.R) + (size_t)(j0 + c0) * a.ld + i;
-#pragma unroll
-          for (int c = 0; c < kTileN / 2; ++c) {
-            if (c < ncol) {
-              const float r = xs[c * kTileM] - d[c];
-              const __nv_bfloat16 rb16 = __float2bfloat16_rn(r);
-              rp[(size_t)c * a.ld] = rb16;
-              const float rr = __bfloat162float(rb16);
-              s2 = fmaf(rr, rr, s2);
-              d[c] = rr;
-            }
-          }
-        }
+      for (int c = 0; c < kTileN / 2; ++c) {
+        const float r = xs[c * kTileM] - d[c];
+        d[c] = F32 ? r : __bfloat162float(__float2bfloat16_rn(r));
+        if (c < ncol && i < a.ld) s2 = fmaf(d[c], d[c], s2);
       }
       if (prow) {
         // Partial of row i over this CTA's tiles, in tile order, from the
@@ -379,9 +291,29 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a, con
         if (quarter == 0 && rb == 0) cc1 += (double)cv * (double)cv;
       }
       acc2 += (double)s2;
-      __syncwarp();
-      if (lane == 0) mbar_arrive(bars + BAR_X_EMPTY + xb);
+      // Every epilogue warp has read its X values: the buffer now takes the
+      // tile of R (float32 in place, or bfloat16 packed at its start), which
+      // goes to global memory by one tensor store.  The warps decide
+      // together whether to go on, so none is left at a named barrier.
+      if (!collective_ok(ok)) break;
+      if (F32) {
+#pragma unroll
+        for (int c = 0; c < kTileN / 2; ++c) xs[c * kTileM] = d[c];
+      } else {
+        __nv_bfloat16* rs = reinterpret_cast<__nv_bfloat16*>(sX + (size_t)xb * kTileN * kTileM) +
+                            (size_t)c0 * kTileM + row_in;
+#pragma unroll
+        for (int c = 0; c < kTileN / 2; ++c) rs[c * kTileM] = __float2bfloat16_rn(d[c]);
+      }
+      fence_proxy_async_shared();
+      named_bar(3, kEpiWarps * 32);
+      if (ew == 0 && lane == 0) {
+        tc::tma_store_2d(&tmR, rb * kTileM, (int)j0, sX + (size_t)xb * kTileN * kTileM);
+        tc::bulk_wait_read_all();
+        mbar_arrive(bars + BAR_X_EMPTY + xb);
+      }
     }
+    if (ew == 0 && lane == 0) tc::bulk_wait_all();
     // A CTA without tiles still owns its partial rows: they are zero.
     if (prow && ntile_cta == 0)
       for (int rb = 0; rb < a.row_blocks; ++rb)
@@ -403,10 +335,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a, con
   if (warp == 1 && lane == 0 && issued > 0) {
     mbar_wait_bounded(bars + BAR_A_EMPTY + ((issued - 1) & 1), (uint32_t)(((issued - 1) >> 1) & 1), err, tmo);
   }
-  tc_fence_before();
+  tc::fence_before();
   __syncthreads();
-  tc_fence_after();
-  if (warp == 1) tmem_dealloc(tmem, kTmemCols);
+  tc::fence_after();
+  if (warp == 1) tc::tmem_dealloc(tmem, kTmemCols);
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int w = 0; w < kEpiWarps; ++w) t += red[w];
@@ -506,20 +438,6 @@ size_t refresh_tc_workspace_bytes(int M, int ld, int64_t N, int K, bool f32) {
 
 int refresh_tc_grid() { return sm_count_tc(); }
 
-// cuTensorMapEncodeTiled from the driver, through the runtime's entry-point query.
-static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q{};
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  });
-  return fn;
-}
-
 template <typename T, bool F32>
 static cudaError_t launch_tc(const float* X, void* R, const float* B, const float* C, int M, int ld, int64_t N,
                              int K, void* workspace, double* part, float* P1, double* CC1, int* err,
@@ -551,23 +469,31 @@ static cudaError_t launch_tc(const float* X, void* R, const float* B, const floa
   a.row_blocks = row_blocks;
   a.col_tiles = col_tiles;
   a.timeout_ns = timeout_ns;
-  // X as a 2-D float32 tensor: rows (ld, contiguous) x columns (N), row stride
-  // ld*4 bytes (ld is a multiple of 16, X 256-byte aligned), box 128 x 64.
-  PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
-  if (!encode) return cudaErrorNotSupported;
-  CUtensorMap tmX;
-  const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)N};
-  const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
-  const cuuint32_t box[2] = {(cuuint32_t)kTileM, (cuuint32_t)kTileN};
-  const cuuint32_t estr[2] = {1, 1};
-  if (encode(&tmX, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(X), dims, strides, box, estr,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
-             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+  // X and R as 2-D tensors: rows (ld, contiguous) x columns (N), column
+  // stride ld elements (ld is a multiple of 16, both 256-byte aligned), box
+  // 128 x 64; R is float32 or bfloat16.
+  CUtensorMap tmX, tmR;
+  if (!encode_f32_colmajor(&tmX, X, ld, N, ld, kTileM, kTileN, CU_TENSOR_MAP_SWIZZLE_NONE))
     return cudaErrorInvalidValue;
+  if (F32) {
+    if (!encode_f32_colmajor(&tmR, R, ld, N, ld, kTileM, kTileN, CU_TENSOR_MAP_SWIZZLE_NONE))
+      return cudaErrorInvalidValue;
+  } else {
+    PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+    if (!encode) return cudaErrorNotSupported;
+    const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)N};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)kTileM, (cuuint32_t)kTileN};
+    const cuuint32_t estr[2] = {1, 1};
+    if (encode(&tmR, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, R, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
   const size_t smem = tc_smem(Kp, (int)sizeof(T)).total;
   e = cudaFuncSetAttribute(refresh_tc_kernel<F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  refresh_tc_kernel<F32><<<sms, kTcThreads, smem, s>>>(a, tmX);
+  refresh_tc_kernel<F32><<<sms, kTcThreads, smem, s>>>(a, tmX, tmR);
   return cudaGetLastError();
 }
 

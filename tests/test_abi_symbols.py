@@ -81,6 +81,7 @@ def test_host_side_argument_checks_need_no_gpu(lib):
 
 @pytest.mark.parametrize("change", [
     dict(flags=1 << 12),                                             # unknown flag bit
+    dict(flags=4, order=2),                                          # a flag bit this library no longer takes
     dict(flags=8 | 16),                                              # eager and lazy write-back together
     dict(inner_c=2),                                                 # inner repeats outside the batched order
     dict(order=2, inner_b=65),                                       # more than 64 repeats
