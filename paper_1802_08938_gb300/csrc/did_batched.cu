@@ -72,8 +72,9 @@ namespace {
 constexpr int kMaxK = 64;             // tensor-memory budget of the update pass
 constexpr int kTcThreads = 384;       // warp 0 producer, warp 1 MMA, 2-3 idle, 4-11 split / epilogue
 constexpr int kWorkWarps = 8;
-constexpr int kGStages = 3;
 constexpr int kGChunk = 32;           // rows of R_s per g stage (128 bytes of a column)
+constexpr int kGMaxRing = 8;          // most stages of a ring of the g pass
+constexpr int kURingMax = 8;          // most stages of the R ring of the update pass
 constexpr uint32_t kTmemCols = 512;
 // Both tensor-core kernels take all 512 TMEM columns, so two of their CTAs
 // must never share an SM: every launch asks for more than half of an SM's
@@ -93,9 +94,14 @@ __host__ __device__ __forceinline__ size_t tiled2(int r, int c, int kp) {
 }
 
 // The six products (i, j), i + j <= 2, of two three-term splits.
-__constant__ const int kProdA[6] = {0, 0, 1, 0, 1, 2};
-__constant__ const int kProdB[6] = {0, 1, 0, 2, 1, 0};
 constexpr int kProds = 6;
+__host__ __device__ constexpr int prod_a(int pr) { return pr == 2 || pr == 4 ? 1 : (pr == 5 ? 2 : 0); }
+__host__ __device__ constexpr int prod_b(int pr) { return pr == 1 || pr == 4 ? 1 : (pr == 3 ? 2 : 0); }
+
+// Shared-memory descriptors differ only in their start address field (bits
+// 0-13, address >> 4): a descriptor is advanced by adding the byte offset >> 4
+// (operands lie below 256 KB of shared memory, so the field never carries).
+__device__ __forceinline__ uint64_t desc_add(uint64_t d, uint32_t bytes) { return d + (uint64_t)(bytes >> 4); }
 
 // Three bfloat16 terms of v, packed in pairs along K: word w of term p holds
 // elements 2w (low half) and 2w + 1 (high half).
@@ -121,13 +127,13 @@ struct BPlan {
   int nt;                 // columns per g tile (<= 256)
   int64_t gtiles;
   int mchunks;            // ceil(ld / 32)
-  int ggrid;
-  size_t gstage, gsmem;
+  int ggrid, grs, gbs;
+  size_t grstage, gbstage, gsmem;
   // update pass
   int nu;                 // columns per update tile (32 or 64)
   int64_t utiles;
-  int RB, Q, units, ugrid, ustages;
-  size_t ustage, usmem;
+  int RB, Q, units, ugrid, urs, uzs;
+  size_t urstage, uzstage, usmem;
   // solve
   int sgrid, npairs;
 };
@@ -158,11 +164,18 @@ bool make_plan(int ld, int64_t N, int K, BPlan* p) {
   P.gtiles = (N + P.nt - 1) / P.nt;
   P.mchunks = (ld + kGChunk - 1) / kGChunk;
   P.ggrid = (int)std::min<int64_t>(sms, P.gtiles);
-  P.gstage = al1024((size_t)P.nt * 128 + (size_t)P.KN * 192);
-  P.gsmem = std::max(kMinSmem, kGStages * P.gstage + (size_t)P.KN * 256 * 4 + 1024 + 256);
+  P.grstage = al1024((size_t)P.nt * 128);
+  P.gbstage = al1024((size_t)P.KN * 192);
+  {
+    const size_t fixed = (size_t)P.KN * 256 * 4 + 1024 + 1024;   // running sums, alignment, barriers
+    P.gbs = 3;
+    P.grs = (int)std::min<size_t>(kGMaxRing, (227 * 1024 - fixed - P.gbs * P.gbstage) / P.grstage);
+    if (P.grs < 2) return false;
+    P.gsmem = std::max(kMinSmem, P.grs * P.grstage + P.gbs * P.gbstage + fixed);
+  }
   // update pass: 64-column tiles where tensor memory holds them, else 32
-  // (columns: two accumulators, two E' buffers of three terms, W, three Y terms)
-  auto tmem_cols = [&](int nu) { return 2 * nu + 3 * nu + P.KN + 3 * P.Z16 / 2; };
+  // (columns: two accumulators, two E' buffers of three terms, two W sets, three Y terms)
+  auto tmem_cols = [&](int nu) { return 2 * nu + 3 * nu + 2 * P.KN + 3 * P.Z16 / 2; };
   P.nu = tmem_cols(64) <= (int)kTmemCols ? 64 : 32;
   if (tmem_cols(P.nu) > (int)kTmemCols) return false;
   P.utiles = (N + P.nu - 1) / P.nu;
@@ -189,16 +202,17 @@ bool make_plan(int ld, int64_t N, int K, BPlan* p) {
   P.Q = bestQ;
   P.units = P.RB * P.Q;
   P.ugrid = std::min(sms, P.units);
-  const size_t fixed = 1024 + 512 + (size_t)P.KN * 128 * 4;   // alignment, barriers, W running sums
-  P.ustage = al1024((size_t)P.nu * 128 * 4 + (size_t)3 * P.nu * P.Z16 * 2 + (size_t)3 * P.KN * P.nu * 2);
-  P.ustages = 0;
-  for (int s = 4; s >= 2; --s)
-    if (s * P.ustage + fixed <= 227 * 1024) {
-      P.ustages = s;
-      break;
-    }
-  if (P.ustages == 0) return false;
-  P.usmem = std::max(kMinSmem, P.ustages * P.ustage + fixed);
+  {
+    const size_t fixed = 1024 + 1024 + (size_t)P.KN * 128 * 4;   // alignment, barriers, W running sums
+    P.urstage = (size_t)P.nu * 128 * 4;
+    P.uzstage = al1024((size_t)3 * P.nu * P.Z16 * 2 + (size_t)3 * P.KN * P.nu * 2);
+    P.uzs = 3;
+    while (P.uzs > 2 && fixed + P.uzs * P.uzstage + 3 * P.urstage > 227 * 1024) --P.uzs;
+    const size_t left = 227 * 1024 - fixed - P.uzs * P.uzstage;
+    P.urs = (int)std::min<size_t>(kURingMax, left / P.urstage);
+    if (P.urs < 3) return false;
+    P.usmem = std::max(kMinSmem, P.urs * P.urstage + P.uzs * P.uzstage + fixed);
+  }
   P.sgrid = 2 * sms;
   P.npairs = K * (K + 1) / 2;
   *p = P;
@@ -235,13 +249,23 @@ struct GArgs {
   float* g;          // [N][K]: g_j contiguous
   int* err;
   int ld, K, KN, nt, mchunks;
+  int rs, bs;        // stages of the R chunk ring and the B chunk ring
   int64_t N, gtiles;
-  size_t gstage;
+  size_t rstage, bstage;
   uint64_t timeout_ns;
 };
 
-enum { G_FULL = 0, G_EMPTY = kGStages, G_SREADY = 2 * kGStages, G_SFREE = G_SREADY + 2, G_ACCFULL = G_SFREE + 2,
-       G_ACCEMPTY = G_ACCFULL + 2, G_DRAIN = G_ACCEMPTY + 2, G_NBARS };
+// Barriers of the g pass (counts in brackets).  R chunks and B chunks have
+// rings of their own: an R chunk is free once the split warps have read it
+// into registers, a B chunk once its MMAs are done.
+//   RFULL[r] (1, tx), REMPTY[r] (8)    R chunk ring
+//   BFULL[b] (1, tx), BEMPTY[b] (1)    B chunk ring (commit)
+//   SREADY[x] (8), SFREE[x] (1)        TMEM staging buffers of the split terms
+//   ACCFULL[x] (1), ACCEMPTY[x] (8)    accumulator sets of alternate groups
+//   DRAIN (1)
+enum { G_RFULL = 0, G_REMPTY = kGMaxRing, G_BFULL = 2 * kGMaxRing, G_BEMPTY = 3 * kGMaxRing,
+       G_SREADY = 4 * kGMaxRing, G_SFREE = G_SREADY + 2, G_ACCFULL = G_SFREE + 2, G_ACCEMPTY = G_ACCFULL + 2,
+       G_DRAIN = G_ACCEMPTY + 2, G_NBARS };
 
 // Chunks of one accumulation group: the tensor cores sum a group's products
 // in a TMEM accumulator, and the split warps add the group totals in float32
@@ -253,7 +277,9 @@ constexpr int kGGroup = 4;
 __global__ void __launch_bounds__(kTcThreads, 1) g_kernel(GArgs a, const __grid_constant__ CUtensorMap tmR) {
   extern __shared__ unsigned char sm_raw[];
   unsigned char* sm = align1024(sm_raw);
-  float* gsum = reinterpret_cast<float*>(sm + kGStages * a.gstage);          // [KN][256] running sums
+  unsigned char* rring = sm;                                                   // R chunks
+  unsigned char* bring = sm + (size_t)a.rs * a.rstage;                         // B chunks
+  float* gsum = reinterpret_cast<float*>(bring + (size_t)a.bs * a.bstage);     // [KN][256] running sums
   uint64_t* bars = reinterpret_cast<uint64_t*>(gsum + (size_t)a.KN * 256);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + G_NBARS);
   int* shared_flags = reinterpret_cast<int*>(tmem_slot + 4);   // [0] MMA chunks issued
@@ -264,7 +290,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) g_kernel(GArgs a, const __grid_
   if (threadIdx.x == 0) {
     shared_flags[0] = 0;
     for (int i = 0; i < G_NBARS; ++i) {
-      const bool per_warp = i == G_SREADY || i == G_SREADY + 1 || i == G_ACCEMPTY || i == G_ACCEMPTY + 1;
+      const bool per_warp = (i >= G_REMPTY && i < G_REMPTY + kGMaxRing) || i == G_SREADY || i == G_SREADY + 1 ||
+                            i == G_ACCEMPTY || i == G_ACCEMPTY + 1;
       mbar_init(bars + i, per_warp ? kWorkWarps : 1);
     }
   }
@@ -286,27 +313,37 @@ __global__ void __launch_bounds__(kTcThreads, 1) g_kernel(GArgs a, const __grid_
   int* err = a.err;
   const uint64_t tmo = a.timeout_ns;
 
-  if (warp == 0) {
+  if (warp == 0 || warp == 3) {
+    // producers: warp 0 the R chunks (2-D TMA, 128-byte swizzle), warp 3 the
+    // B chunks (bulk copies from L2)
     if (lane == 0) {
+      const bool rprod = warp == 0;
+      const int ring = rprod ? a.rs : a.bs;
+      uint64_t* full = bars + (rprod ? G_RFULL : G_BFULL);
+      uint64_t* empty = bars + (rprod ? G_REMPTY : G_BEMPTY);
       int64_t c = 0;
       for (; c < total; ++c) {
         const int64_t ti = c / a.mchunks;
         const int mc = (int)(c % a.mchunks);
         const int64_t tile = blockIdx.x + ti * gridDim.x;
-        const int s = (int)(c % kGStages);
-        if (c >= kGStages && !tc::wait(bars + G_EMPTY + s, (uint32_t)(((c / kGStages) - 1) & 1), err, tmo)) break;
-        unsigned char* st = sm + (size_t)s * a.gstage;
-        mbar_arrive_expect_tx(bars + G_FULL + s, (uint32_t)(rbytes + (size_t)KN * 192));
-        tc::tma_load_2d(st, &tmR, mc * kGChunk, (int)(tile * a.nt), bars + G_FULL + s);
-        bulk_load(st + rbytes, a.Bg + (size_t)mc * 3 * KN * kGChunk, (uint32_t)KN * 192, bars + G_FULL + s);
+        const int s = (int)(c % ring);
+        if (c >= ring && !tc::wait(empty + s, (uint32_t)(((c / ring) - 1) & 1), err, tmo)) break;
+        if (rprod) {
+          mbar_arrive_expect_tx(full + s, (uint32_t)rbytes);
+          tc::tma_load_2d(rring + (size_t)s * a.rstage, &tmR, mc * kGChunk, (int)(tile * a.nt), full + s);
+        } else {
+          mbar_arrive_expect_tx(full + s, (uint32_t)KN * 192);
+          bulk_load(bring + (size_t)s * a.bstage, a.Bg + (size_t)mc * 3 * KN * kGChunk, (uint32_t)KN * 192, full + s);
+        }
       }
       // copies still in flight complete before the CTA exits (bounded)
-      for (int64_t d = std::max<int64_t>(0, c - kGStages); d < c; ++d)
-        mbar_wait_bounded(bars + G_FULL + (d % kGStages), (uint32_t)((d / kGStages) & 1), err, tmo);
+      for (int64_t d = std::max<int64_t>(0, c - ring); d < c; ++d)
+        mbar_wait_bounded(full + (d % ring), (uint32_t)((d / ring) & 1), err, tmo);
     }
   } else if (warp == 1) {
     if (lane == 0) {
       const uint32_t idesc = tc::instr_desc_bf16(128, KN);
+      const uint64_t bdesc_ring = tc::smem_desc(smem_u32(bring), 128u, (uint32_t)kGChunk * 16u);
       int64_t c = 0;
       for (; c < total; ++c) {
         const int64_t ti = c / a.mchunks;
@@ -315,25 +352,29 @@ __global__ void __launch_bounds__(kTcThreads, 1) g_kernel(GArgs a, const __grid_
         const int x = (int)(gi & 1);
         const bool gfirst = mc % kGGroup == 0;
         const bool glast = mc % kGGroup == kGGroup - 1 || mc == a.mchunks - 1;
-        const int s = (int)(c % kGStages), b = (int)(c & 1);
-        if (!tc::wait(bars + G_FULL + s, (uint32_t)((c / kGStages) & 1), err, tmo)) break;
+        const int s = (int)(c % a.bs), b = (int)(c & 1);
+        if (!tc::wait(bars + G_BFULL + s, (uint32_t)((c / a.bs) & 1), err, tmo)) break;
         if (!tc::wait(bars + G_SREADY + b, (uint32_t)((c >> 1) & 1), err, tmo)) break;
         if (gfirst && gi >= 2 && !tc::wait(bars + G_ACCEMPTY + x, (uint32_t)(((gi >> 1) - 1) & 1), err, tmo)) break;
         tc::fence_after();
-        const uint32_t sB = smem_u32(sm + (size_t)s * a.gstage + rbytes);
+        const uint64_t bd0 = desc_add(bdesc_ring, (uint32_t)((size_t)s * a.bstage));
+        const uint32_t pterm = (uint32_t)(KN * kGChunk * 2);    // bytes of one term of the B chunk
+#pragma unroll
         for (int h = 0; h < 2; ++h) {
-          if (h * 128 >= a.nt) break;
-          for (int pr = 0; pr < kProds; ++pr) {
-            const uint32_t acol = staging(b, h) + (uint32_t)(16 * kProdA[pr]);
-            const uint32_t boff = (uint32_t)(kProdB[pr] * KN * kGChunk * 2);
-            for (int kk = 0; kk < kGChunk / 16; ++kk) {
-              const uint64_t bd = tc::smem_desc(sB + boff + (uint32_t)kk * 256u, 128u, (uint32_t)kGChunk * 16u);
-              tc::mma_bf16_tmem_a(tmem + accum(x, h), tmem + acol + (uint32_t)kk * 8u, bd, idesc,
-                                  (!gfirst || pr > 0 || kk > 0) ? 1u : 0u);
+          if (h * 128 < a.nt) {
+            const uint32_t d = tmem + accum(x, h);
+            const uint32_t a0 = tmem + staging(b, h);
+#pragma unroll
+            for (int pr = 0; pr < kProds; ++pr) {
+#pragma unroll
+              for (int kk = 0; kk < kGChunk / 16; ++kk)
+                tc::mma_bf16_tmem_a(d, a0 + (uint32_t)(16 * prod_a(pr) + 8 * kk),
+                                    desc_add(bd0, (uint32_t)(prod_b(pr) * pterm + kk * 256)), idesc,
+                                    (!gfirst || pr > 0 || kk > 0) ? 1u : 0u);
             }
           }
         }
-        tc::mma_commit(bars + G_EMPTY + s);
+        tc::mma_commit(bars + G_BEMPTY + s);
         tc::mma_commit(bars + G_SFREE + b);
         if (glast) tc::mma_commit(bars + G_ACCFULL + x);
       }
@@ -345,29 +386,60 @@ __global__ void __launch_bounds__(kTcThreads, 1) g_kernel(GArgs a, const __grid_
     const int jl = half * 128 + quarter * 32 + lane;     // column within the tile (TMEM lane jl % 128)
     const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
     bool ok = true;
+    int drained = 0;    // groups of the current tile added into the sums
+    // Add group gl of tile ti (accumulator set gi & 1) into this column's sums.
+    auto drain = [&](int64_t ti, int gl) -> bool {
+      if (gl != drained) return true;
+      const int64_t gi = ti * ngroups + gl;
+      const int x = (int)(gi & 1);
+      bool good = tc::wait(bars + G_ACCFULL + x, (uint32_t)((gi >> 1) & 1), err, tmo);
+      good = __all_sync(0xffffffffu, good);
+      if (!good) return false;
+      tc::fence_after();
+      for (int k0 = 0; k0 < KN; k0 += 16) {
+        float v[16];
+        tc::tmem_ld<16>(tmem + lane_base + accum(x, half) + (uint32_t)k0, v);
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          float* q = gsum + (size_t)(k0 + u) * 256 + jl;
+          *q = gl == 0 ? v[u] : *q + v[u];
+        }
+      }
+      tc::fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bars + G_ACCEMPTY + x);
+      ++drained;
+      return true;
+    };
     for (int64_t c = 0; c < total && ok; ++c) {
       const int64_t ti = c / a.mchunks;
       const int mc = (int)(c % a.mchunks);
       const int64_t tile = blockIdx.x + ti * gridDim.x;
-      const int64_t gi = ti * ngroups + mc / kGGroup;
-      const int x = (int)(gi & 1);
-      const bool glast = mc % kGGroup == kGGroup - 1 || mc == a.mchunks - 1;
-      const int s = (int)(c % kGStages), b = (int)(c & 1);
-      ok = tc::wait(bars + G_FULL + s, (uint32_t)((c / kGStages) & 1), err, tmo);
-      if (ok && c >= 2) ok = tc::wait(bars + G_SFREE + b, (uint32_t)(((c >> 1) - 1) & 1), err, tmo);
+      const int s = (int)(c % a.rs), b = (int)(c & 1);
+      ok = tc::wait(bars + G_RFULL + s, (uint32_t)((c / a.rs) & 1), err, tmo);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) break;
+      // Row jl of the swizzled tile: logical 16-byte chunk q sits at chunk q ^ (jl % 8).
+      float4 v[8];
+      const unsigned char* row = rring + (size_t)s * a.rstage + (size_t)jl * 128;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (jl < a.nt) v[q] = *reinterpret_cast<const float4*>(row + ((q ^ (jl & 7)) << 4));
+      }
+      // the chunk is in registers: its buffer goes back to the producer
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bars + G_REMPTY + s);
+      uint32_t t0[16], t1[16], t2[16];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        split_pair(v[q].x, v[q].y, t0[2 * q], t1[2 * q], t2[2 * q]);
+        split_pair(v[q].z, v[q].w, t0[2 * q + 1], t1[2 * q + 1], t2[2 * q + 1]);
+      }
+      if (c >= 2) ok = tc::wait(bars + G_SFREE + b, (uint32_t)(((c >> 1) - 1) & 1), err, tmo);
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) break;
       tc::fence_after();
-      // Row jl of the swizzled tile: logical 16-byte chunk q sits at chunk q ^ (jl % 8).
-      uint32_t t0[16], t1[16], t2[16];
-      const unsigned char* row = sm + (size_t)s * a.gstage + (size_t)jl * 128;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (jl < a.nt) v = *reinterpret_cast<const float4*>(row + ((q ^ (jl & 7)) << 4));
-        split_pair(v.x, v.y, t0[2 * q], t1[2 * q], t2[2 * q]);
-        split_pair(v.z, v.w, t0[2 * q + 1], t1[2 * q + 1], t2[2 * q + 1]);
-      }
       const uint32_t col = staging(b, half);
       tc::tmem_st_u16(tmem + lane_base + col, t0);
       tc::tmem_st_u16(tmem + lane_base + col + 16, t1);
@@ -376,32 +448,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) g_kernel(GArgs a, const __grid_
       tc::fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(bars + G_SREADY + b);
-      if (glast) {
-        // the group's total into the running sums of this column (the first
-        // group of a tile starts them)
-        ok = tc::wait(bars + G_ACCFULL + x, (uint32_t)((gi >> 1) & 1), err, tmo);
-        ok = __all_sync(0xffffffffu, ok);
-        if (!ok) break;
-        tc::fence_after();
-        const bool gfirst_of_tile = mc < kGGroup;
-        for (int k0 = 0; k0 < KN; k0 += 16) {
-          float v[16];
-          tc::tmem_ld<16>(tmem + lane_base + accum(x, half) + (uint32_t)k0, v);
-#pragma unroll
-          for (int u = 0; u < 16; ++u) {
-            float* q = gsum + (size_t)(k0 + u) * 256 + jl;
-            *q = gfirst_of_tile ? v[u] : *q + v[u];
-          }
-        }
-        tc::fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(bars + G_ACCEMPTY + x);
-        if (mc == a.mchunks - 1) {
+      // Group totals are added one group later (while the next group's MMAs
+      // run, its products long done); the tile's last groups at its end.
+      const int gl = mc / kGGroup, pos = mc % kGGroup;
+      if (pos == 1 && gl >= 1) ok = drain(ti, gl - 1);
+      if (ok && mc == a.mchunks - 1) {
+        while (ok && drained < ngroups) ok = drain(ti, drained);
+        if (ok) {
           const int64_t j = tile * a.nt + jl;
           if (jl < a.nt && j < a.N) {
             float* gj = a.g + (size_t)j * a.K;
             for (int k = 0; k < a.K; ++k) gj[k] = gsum[(size_t)k * 256 + jl];
           }
+          drained = 0;
         }
       }
     }
@@ -566,19 +625,35 @@ struct UArgs {
   float* Wp;           // [units][KN][128] partial rows of W = E' C'^T
   double* part_n;      // [grid] partial ||E'||^2
   int* err;
-  int ld, K, KN, Z16, nu, RB, Q, units, stages;
+  int ld, K, KN, Z16, nu, RB, Q, units;
+  int rs, zs;          // stages of the R tile ring and of the Z / C'^T tile ring
   int64_t N, utiles;
-  size_t ustage;
+  size_t rstage, zstage;
   uint64_t timeout_ns;
 };
 
-enum { U_FULL = 0, U_EMPTY = 4, U_ACCFULL = 8, U_ACCEMPTY = 10, U_EREADY = 12, U_EFREE = 14, U_YREADY = 16,
-       U_WFULL = 17, U_WEMPTY = 18, U_DRAIN = 19, U_NBARS = 20 };
+// Barriers of the update pass (counts in brackets).  Tiles of R_s and the
+// operand tiles Z, C'^T have rings of their own: an R tile is held from its
+// load until the store of E' has read it, an operand tile only until its W
+// products are done.
+//   RFULL[r] (1, tx), REMPTY[r] (1)   R ring (the store warp releases)
+//   EPIDONE[r] (8)                    the tile of E' in R buffer r is complete
+//   ZFULL[z] (1, tx), ZEMPTY[z] (1)   operand ring (W commit releases)
+//   ACCFULL[x] (1), ACCEMPTY[x] (8)   accumulators of Y Z
+//   EREADY[x] (8), EFREE[x] (1)       E' buffers (three terms each) in TMEM
+//   YREADY (8)                        the Y row block of the next unit is in TMEM
+//   WFULL[w] (1), WEMPTY[w] (8)       W sets of alternate groups of tiles
+//   DRAIN (1)
+constexpr int kURing = kURingMax;
+enum { U_RFULL = 0, U_REMPTY = kURing, U_EPIDONE = 2 * kURing, U_ZFULL = 3 * kURing, U_ZEMPTY = 3 * kURing + 4,
+       U_ACCFULL = 3 * kURing + 8, U_ACCEMPTY = U_ACCFULL + 2, U_EREADY = U_ACCEMPTY + 2, U_EFREE = U_EREADY + 2,
+       U_YREADY = U_EFREE + 2, U_WFULL = U_YREADY + 1, U_WEMPTY = U_WFULL + 2, U_DRAIN = U_WEMPTY + 2, U_NBARS };
 
 // Tiles of one W accumulation group: the tensor cores sum a group's
-// contributions to the unit's W rows in TMEM, and the epilogue warps add the
-// group totals in float32 (round to nearest) in shared memory, which keeps
-// the accumulator chains short over the unit's many columns.
+// contributions to the unit's W rows in one of two TMEM sets, and the
+// epilogue warps add each group's total in float32 (round to nearest) in
+// shared memory one tile later, which keeps the accumulator chains short over
+// the unit's many columns without stalling the pipeline.
 constexpr int kWGroup = 8;
 
 __device__ __forceinline__ void unit_tiles(const UArgs& a, int u, int& rb, int64_t& t0, int64_t& t1) {
@@ -592,7 +667,9 @@ template <int NU>
 __global__ void __launch_bounds__(kTcThreads, 1) update_kernel(UArgs a, const __grid_constant__ CUtensorMap tmR) {
   extern __shared__ unsigned char sm_raw[];
   unsigned char* sm = align1024(sm_raw);
-  float* wsum = reinterpret_cast<float*>(sm + (size_t)a.stages * a.ustage);   // [KN][128] the unit's W rows
+  unsigned char* rring = sm;                                               // R tiles [nu][128] float32
+  unsigned char* zring = sm + (size_t)a.rs * a.rstage;                     // Z and C'^T tiles
+  float* wsum = reinterpret_cast<float*>(zring + (size_t)a.zs * a.zstage);  // [KN][128] the unit's W rows
   uint64_t* bars = reinterpret_cast<uint64_t*>(wsum + (size_t)a.KN * 128);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + U_NBARS);
   int* shared_flags = reinterpret_cast<int*>(tmem_slot + 4);   // [0] MMA issued anything
@@ -600,28 +677,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) update_kernel(UArgs a, const __
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int nu = NU;
-  const int KN = a.KN, Z16 = a.Z16, S = a.stages;
+  const int KN = a.KN, Z16 = a.Z16, RS = a.rs, ZS = a.zs;
   const size_t rbytes = (size_t)nu * 128 * 4;
   const size_t zpart = (size_t)nu * Z16 * 2;      // bytes of one term of the Z tile
   const size_t cpart = (size_t)KN * nu * 2;       // bytes of one term of the C'^T tile
   const size_t zbytes = 3 * zpart, cbytes = 3 * cpart;
   // TMEM columns: two accumulators, two E' buffers (three terms of nu/2
-  // columns each), the unit's W rows, and the three terms of the Y row block.
-  const uint32_t WACC = 5 * nu, Y0 = 5 * nu + KN;
+  // columns each), two W sets, and the three terms of the Y row block.
+  const uint32_t W0 = 5 * nu, Y0 = 5 * nu + 2 * KN;
   auto ACC = [&](int x) { return (uint32_t)(x * nu); };
   auto EP = [&](int x, int p) { return (uint32_t)(2 * nu + x * (3 * nu / 2) + p * (nu / 2)); };
+  auto WS = [&](int w) { return W0 + (uint32_t)(w * KN); };
   auto YP = [&](int p) { return Y0 + (uint32_t)(p * (Z16 / 2)); };
 
   if (threadIdx.x == 0) {
     shared_flags[0] = 0;
-    shared_flags[1] = 0;
     for (int i = 0; i < U_NBARS; ++i) {
-      uint32_t cnt = 1;
-      if (i >= U_EMPTY && i < U_EMPTY + 4) cnt = 2;                      // W commit + store read
-      if (i == U_ACCEMPTY || i == U_ACCEMPTY + 1 || i == U_EREADY || i == U_EREADY + 1 || i == U_YREADY ||
-          i == U_WEMPTY)
-        cnt = kWorkWarps;
-      mbar_init(bars + i, cnt);
+      const bool per_warp = (i >= U_EPIDONE && i < U_EPIDONE + kURing) || (i >= U_ACCEMPTY && i < U_ACCEMPTY + 2) ||
+                            (i >= U_EREADY && i < U_EREADY + 2) || i == U_YREADY ||
+                            (i >= U_WEMPTY && i < U_WEMPTY + 2);
+      mbar_init(bars + i, per_warp ? kWorkWarps : 1);
     }
   }
   fence_mbar_init();
@@ -633,10 +708,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) update_kernel(UArgs a, const __
   int* err = a.err;
   const uint64_t tmo = a.timeout_ns;
   const int nunits_cta = a.units > (int)blockIdx.x ? (a.units - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  // W groups of a unit of n tiles: tile rel belongs to group rel / kWGroup.
+  auto ngroups = [&](int64_t n) { return (n + kWGroup - 1) / kWGroup; };
 
-  if (warp == 0) {
-    // ------------------------------------------------------------ producer
+  if (warp == 0 || warp == 3) {
+    // ----------------------------------------------------------- producers
+    // warp 0: R tiles (2-D TMA); warp 3: the Z and C'^T tiles (bulk copies)
     if (lane == 0) {
+      const bool rprod = warp == 0;
+      const int ring = rprod ? RS : ZS;
+      uint64_t* full = bars + (rprod ? U_RFULL : U_ZFULL);
+      uint64_t* empty = bars + (rprod ? U_REMPTY : U_ZEMPTY);
       int64_t i = 0;
       bool ok = true;
       for (int ui = 0; ui < nunits_cta && ok; ++ui) {
@@ -644,51 +726,58 @@ __global__ void __launch_bounds__(kTcThreads, 1) update_kernel(UArgs a, const __
         int64_t t0, t1;
         unit_tiles(a, (int)blockIdx.x + ui * (int)gridDim.x, rb, t0, t1);
         for (int64_t t = t0; t < t1; ++t, ++i) {
-          const int s = (int)(i % S);
-          if (i >= S && !tc::wait(bars + U_EMPTY + s, (uint32_t)(((i / S) - 1) & 1), err, tmo)) {
+          const int s = (int)(i % ring);
+          if (i >= ring && !tc::wait(empty + s, (uint32_t)(((i / ring) - 1) & 1), err, tmo)) {
             ok = false;
             break;
           }
-          unsigned char* st = sm + (size_t)s * a.ustage;
-          mbar_arrive_expect_tx(bars + U_FULL + s, (uint32_t)(rbytes + zbytes + cbytes));
-          tc::tma_load_2d(st, &tmR, rb * 128, (int)(t * nu), bars + U_FULL + s);
-          bulk_load(st + rbytes, a.Zt + (size_t)t * 3 * nu * Z16, (uint32_t)zbytes, bars + U_FULL + s);
-          bulk_load(st + rbytes + zbytes, a.Ct + (size_t)t * 3 * KN * nu, (uint32_t)cbytes, bars + U_FULL + s);
+          if (rprod) {
+            mbar_arrive_expect_tx(full + s, (uint32_t)rbytes);
+            tc::tma_load_2d(rring + (size_t)s * a.rstage, &tmR, rb * 128, (int)(t * nu), full + s);
+          } else {
+            unsigned char* st = zring + (size_t)s * a.zstage;
+            mbar_arrive_expect_tx(full + s, (uint32_t)(zbytes + cbytes));
+            bulk_load(st, a.Zt + (size_t)t * 3 * nu * Z16, (uint32_t)zbytes, full + s);
+            bulk_load(st + zbytes, a.Ct + (size_t)t * 3 * KN * nu, (uint32_t)cbytes, full + s);
+          }
         }
       }
-      for (int64_t d = std::max<int64_t>(0, i - S); d < i; ++d)
-        mbar_wait_bounded(bars + U_FULL + (d % S), (uint32_t)((d / S) & 1), err, tmo);
+      for (int64_t d = std::max<int64_t>(0, i - ring); d < i; ++d)
+        mbar_wait_bounded(full + (d % ring), (uint32_t)((d / ring) & 1), err, tmo);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------- MMA issue
     if (lane == 0) {
       const uint32_t iU = tc::instr_desc_bf16(128, nu), iW = tc::instr_desc_bf16(128, KN);
+      const uint64_t zdesc_ring = tc::smem_desc(smem_u32(zring), 128u, (uint32_t)Z16 * 16u);
+      const uint64_t cdesc_ring = tc::smem_desc(smem_u32(zring), 128u, (uint32_t)nu * 16u);
       int64_t i = 0;
       bool ok = true;
-      int64_t wg = 0;     // W groups issued so far
+      int64_t wg = 0;     // W groups started so far (set wg & 1)
       // W(i): E'(i) (three terms, TMEM) times C'^T(i) (three terms, shared)
-      // into the W accumulator; rel is the tile's place in its unit of n tiles.
+      // into the current W set; rel is the tile's place in its unit of n tiles.
       auto issue_w = [&](int64_t iw, int64_t rel, int64_t n) -> bool {
-        const int s = (int)(iw % S), x = (int)(iw & 1);
+        const int s = (int)(iw % ZS), x = (int)(iw & 1);
         const bool gfirst = rel % kWGroup == 0;
         const bool glast = rel % kWGroup == kWGroup - 1 || rel == n - 1;
+        const int w = (int)(wg & 1);
         if (!tc::wait(bars + U_EREADY + x, (uint32_t)((iw >> 1) & 1), err, tmo)) return false;
-        if (gfirst && wg > 0 && !tc::wait(bars + U_WEMPTY, (uint32_t)((wg - 1) & 1), err, tmo)) return false;
+        if (gfirst && wg >= 2 && !tc::wait(bars + U_WEMPTY + w, (uint32_t)(((wg >> 1) - 1) & 1), err, tmo))
+          return false;
         tc::fence_after();
-        const uint32_t sC = smem_u32(sm + (size_t)s * a.ustage + rbytes + zbytes);
+        const uint64_t cd0 = desc_add(cdesc_ring, (uint32_t)((size_t)s * a.zstage + zbytes));
+#pragma unroll
         for (int pr = 0; pr < kProds; ++pr) {
-          const uint32_t acol = EP(x, kProdA[pr]);
-          const uint32_t boff = (uint32_t)(kProdB[pr] * cpart);
-          for (int kk = 0; kk < nu / 16; ++kk) {
-            const uint64_t bd = tc::smem_desc(sC + boff + (uint32_t)kk * 256u, 128u, (uint32_t)nu * 16u);
-            tc::mma_bf16_tmem_a(tmem + WACC, tmem + acol + (uint32_t)kk * 8u, bd, iW,
+#pragma unroll
+          for (int kk = 0; kk < nu / 16; ++kk)
+            tc::mma_bf16_tmem_a(tmem + WS(w), tmem + EP(x, prod_a(pr)) + (uint32_t)kk * 8u,
+                                desc_add(cd0, (uint32_t)(prod_b(pr) * cpart + kk * 256)), iW,
                                 (gfirst && pr == 0 && kk == 0) ? 0u : 1u);
-          }
         }
         tc::mma_commit(bars + U_EFREE + x);
-        tc::mma_commit(bars + U_EMPTY + s);
+        tc::mma_commit(bars + U_ZEMPTY + s);
         if (glast) {
-          tc::mma_commit(bars + U_WFULL);
+          tc::mma_commit(bars + U_WFULL + w);
           ++wg;
         }
         return true;
@@ -700,22 +789,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) update_kernel(UArgs a, const __
         if (!tc::wait(bars + U_YREADY, (uint32_t)(ui & 1), err, tmo)) break;
         const int64_t ifirst = i, n = t1 - t0;
         for (int64_t t = t0; t < t1; ++t, ++i) {
-          const int s = (int)(i % S), x = (int)(i & 1);
-          if (!tc::wait(bars + U_FULL + s, (uint32_t)((i / S) & 1), err, tmo)) { ok = false; break; }
+          const int s = (int)(i % ZS), x = (int)(i & 1);
+          if (!tc::wait(bars + U_ZFULL + s, (uint32_t)((i / ZS) & 1), err, tmo)) { ok = false; break; }
           if (i >= 2 && !tc::wait(bars + U_ACCEMPTY + x, (uint32_t)(((i >> 1) - 1) & 1), err, tmo)) {
             ok = false;
             break;
           }
           tc::fence_after();
-          const uint32_t sZ = smem_u32(sm + (size_t)s * a.ustage + rbytes);
+          const uint64_t zd0 = desc_add(zdesc_ring, (uint32_t)((size_t)s * a.zstage));
+          const int ksteps = Z16 / 16;
+#pragma unroll
           for (int pr = 0; pr < kProds; ++pr) {
-            const uint32_t acol = YP(kProdA[pr]);
-            const uint32_t boff = (uint32_t)(kProdB[pr] * zpart);
-            for (int kk = 0; kk < Z16 / 16; ++kk) {
-              const uint64_t bd = tc::smem_desc(sZ + boff + (uint32_t)kk * 256u, 128u, (uint32_t)Z16 * 16u);
-              tc::mma_bf16_tmem_a(tmem + ACC(x), tmem + acol + (uint32_t)kk * 8u, bd, iU,
-                                  (pr > 0 || kk > 0) ? 1u : 0u);
-            }
+            const uint32_t a0 = tmem + YP(prod_a(pr));
+            const uint64_t b0 = desc_add(zd0, (uint32_t)(prod_b(pr) * zpart));
+#pragma unroll
+            for (int kk = 0; kk < kMaxK * 2 / 16; ++kk)
+              if (kk < ksteps)
+                tc::mma_bf16_tmem_a(tmem + ACC(x), a0 + (uint32_t)kk * 8u, desc_add(b0, (uint32_t)kk * 256u), iU,
+                                    (pr > 0 || kk > 0) ? 1u : 0u);
           }
           tc::mma_commit(bars + U_ACCFULL + x);
           shared_flags[0] = 1;
@@ -725,6 +816,36 @@ __global__ void __launch_bounds__(kTcThreads, 1) update_kernel(UArgs a, const __
         if (i > ifirst && !issue_w(i - 1, i - 1 - ifirst, n)) break;
       }
     }
+  } else if (warp == 2) {
+    // ------------------------------------------------------------ store warp
+    // Each finished tile of E' goes back to R_s by one tensor store.  Its
+    // stage is released once the store has read it: the wait for tile i's
+    // read comes after tile i+1's store is issued, so stores overlap.
+    if (lane == 0) {
+      int64_t i = 0;
+      int prev_s = -1;
+      bool ok = true;
+      for (int ui = 0; ui < nunits_cta && ok; ++ui) {
+        int rb;
+        int64_t t0, t1;
+        unit_tiles(a, (int)blockIdx.x + ui * (int)gridDim.x, rb, t0, t1);
+        for (int64_t t = t0; t < t1; ++t, ++i) {
+          const int s = (int)(i % RS);
+          if (!tc::wait(bars + U_EPIDONE + s, (uint32_t)((i / RS) & 1), err, tmo)) {
+            ok = false;
+            break;
+          }
+          tc::tma_store_2d(&tmR, rb * 128, (int)(t * nu), rring + (size_t)s * a.rstage);
+          if (prev_s >= 0) {
+            asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+            mbar_arrive(bars + U_REMPTY + prev_s);
+          }
+          prev_s = s;
+        }
+      }
+      tc::bulk_wait_all();
+      if (prev_s >= 0) mbar_arrive(bars + U_REMPTY + prev_s);
+    }
   } else if (warp >= 4) {
     // --------------------------------------------------------------- epilogue
     const int ew = warp - 4;
@@ -732,20 +853,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) update_kernel(UArgs a, const __
     const int row = quarter * 32 + lane;
     const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
     constexpr int hc = nu / 2;                   // columns of this warp's half of a tile
+    const int kh = KN / 2;                       // W columns of this warp's half
     double acc2 = 0.0;
     bool ok = true;
-    int64_t wgE = 0;    // W groups drained so far
-    // The epilogue warps leave their loops together: a warp that saw a wait
-    // run out raises the shared flag before the first named barrier, every
-    // warp reads it between the two (no warp writes it in between), so all
-    // take the same branch and none is left waiting at a named barrier.
-    auto collective_ok = [&](bool good) -> bool {
-      if (!good && lane == 0) *reinterpret_cast<volatile int*>(&shared_flags[1]) = 1;
-      named_bar(1, kWorkWarps * 32);
-      const int f = *reinterpret_cast<volatile int*>(&shared_flags[1]);
-      named_bar(2, kWorkWarps * 32);
-      return f == 0;
-    };
+    int64_t wgE = 0;    // W groups added into the sums so far
     // Y rows of a row block into TMEM: half 0 stores terms 0 and 1, half 1 term 2.
     auto load_y = [&](int rb) {
       const int m = rb * 128 + row;
@@ -771,6 +882,29 @@ __global__ void __launch_bounds__(kTcThreads, 1) update_kernel(UArgs a, const __
       __syncwarp();
       if (lane == 0) mbar_arrive(bars + U_YREADY);
     };
+    // Add W group wgE (set wgE & 1) into this thread's row sums; the unit's
+    // first group starts them.
+    auto drain_w = [&](bool first_of_unit) -> bool {
+      const int w = (int)(wgE & 1);
+      bool good = tc::wait(bars + U_WFULL + w, (uint32_t)((wgE >> 1) & 1), err, tmo);
+      good = __all_sync(0xffffffffu, good);
+      if (!good) return false;
+      tc::fence_after();
+      for (int k0 = 0; k0 < kh; k0 += 8) {
+        float wv[8];
+        tc::tmem_ld<8>(tmem + lane_base + WS(w) + (uint32_t)(h * kh + k0), wv);
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+          float* q = wsum + (size_t)(h * kh + k0 + v) * 128 + row;
+          *q = first_of_unit ? wv[v] : *q + wv[v];
+        }
+      }
+      tc::fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bars + U_WEMPTY + w);
+      ++wgE;
+      return true;
+    };
     int64_t i = 0;
     if (nunits_cta > 0) {
       int rb;
@@ -783,96 +917,69 @@ __global__ void __launch_bounds__(kTcThreads, 1) update_kernel(UArgs a, const __
       int rb;
       int64_t t0, t1;
       unit_tiles(a, u, rb, t0, t1);
-      for (int64_t t = t0; t < t1; ++t, ++i) {
-        const int s = (int)(i % S), x = (int)(i & 1);
-        bool good = tc::wait(bars + U_ACCFULL + x, (uint32_t)((i >> 1) & 1), err, tmo) &&
-                    tc::wait(bars + U_FULL + s, (uint32_t)((i / S) & 1), err, tmo);
-        good = __all_sync(0xffffffffu, good);
-        if (good) {
-          tc::fence_after();
-          float d[hc];
+      const int64_t n = t1 - t0, wg_first = wgE;
+      for (int64_t t = t0; t < t1 && ok; ++t, ++i) {
+        const int s = (int)(i % RS), x = (int)(i & 1);
+        ok = tc::wait(bars + U_ACCFULL + x, (uint32_t)((i >> 1) & 1), err, tmo) &&
+             tc::wait(bars + U_RFULL + s, (uint32_t)((i / RS) & 1), err, tmo);
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) break;
+        tc::fence_after();
+        float d[hc];
 #pragma unroll
-          for (int c = 0; c < hc; c += 16)
-            tc::tmem_ld<16>(tmem + lane_base + ACC(x) + (uint32_t)(h * hc + c), d + c);
-          tc::fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(bars + U_ACCEMPTY + x);
-          // E' = R_s - Y Z on this thread's row and half of the tile; written
-          // back in place for the store, squared into the norm.
-          float* rt = reinterpret_cast<float*>(sm + (size_t)s * a.ustage) + (size_t)(h * hc) * 128 + row;
-          uint32_t e0[hc / 2], e1[hc / 2], e2[hc / 2];
-          float s2 = 0.f;
+        for (int c = 0; c < hc; c += 16)
+          tc::tmem_ld<16>(tmem + lane_base + ACC(x) + (uint32_t)(h * hc + c), d + c);
+        tc::fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bars + U_ACCEMPTY + x);
+        // E' = R_s - Y Z on this thread's row and half of the tile; written
+        // back in place for the store, squared into the norm.
+        float* rt = reinterpret_cast<float*>(rring + (size_t)s * a.rstage) + (size_t)(h * hc) * 128 + row;
+        uint32_t e0[hc / 2], e1[hc / 2], e2[hc / 2];
+        float s2 = 0.f;
 #pragma unroll
-          for (int c = 0; c < hc; c += 2) {
-            const float ea = rt[(size_t)c * 128] - d[c];
-            const float eb = rt[(size_t)(c + 1) * 128] - d[c + 1];
-            rt[(size_t)c * 128] = ea;
-            rt[(size_t)(c + 1) * 128] = eb;
-            s2 = fmaf(ea, ea, s2);
-            s2 = fmaf(eb, eb, s2);
-            split_pair(ea, eb, e0[c / 2], e1[c / 2], e2[c / 2]);
-          }
-          acc2 += (double)s2;
-          if (i >= 2) good = tc::wait(bars + U_EFREE + x, (uint32_t)(((i >> 1) - 1) & 1), err, tmo);
-          good = __all_sync(0xffffffffu, good);
-          if (good) {
-            tc::fence_after();
-            const uint32_t c0 = (uint32_t)(h * hc / 2);
-            if (hc / 2 == 16) {
-              tc::tmem_st_u16(tmem + lane_base + EP(x, 0) + c0, e0);
-              tc::tmem_st_u16(tmem + lane_base + EP(x, 1) + c0, e1);
-              tc::tmem_st_u16(tmem + lane_base + EP(x, 2) + c0, e2);
-            } else {
-              tc::tmem_st_u8(tmem + lane_base + EP(x, 0) + c0, e0);
-              tc::tmem_st_u8(tmem + lane_base + EP(x, 1) + c0, e1);
-              tc::tmem_st_u8(tmem + lane_base + EP(x, 2) + c0, e2);
-            }
-            tc::tmem_st_wait();
-            tc::fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(bars + U_EREADY + x);
-          }
+        for (int c = 0; c < hc; c += 2) {
+          const float ea = rt[(size_t)c * 128] - d[c];
+          const float eb = rt[(size_t)(c + 1) * 128] - d[c + 1];
+          rt[(size_t)c * 128] = ea;
+          rt[(size_t)(c + 1) * 128] = eb;
+          s2 = fmaf(ea, ea, s2);
+          s2 = fmaf(eb, eb, s2);
+          split_pair(ea, eb, e0[c / 2], e1[c / 2], e2[c / 2]);
         }
-        // the tile of E' goes back to R_s by one tensor store
+        acc2 += (double)s2;
+        // the tile in shared memory is complete for the store warp
         fence_proxy_async_shared();
-        if (!collective_ok(good)) {
-          ok = false;
-          break;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bars + U_EPIDONE + s);
+        if (i >= 2) ok = tc::wait(bars + U_EFREE + x, (uint32_t)(((i >> 1) - 1) & 1), err, tmo);
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) break;
+        tc::fence_after();
+        const uint32_t c0 = (uint32_t)(h * hc / 2);
+        if (hc / 2 == 16) {
+          tc::tmem_st_u16(tmem + lane_base + EP(x, 0) + c0, e0);
+          tc::tmem_st_u16(tmem + lane_base + EP(x, 1) + c0, e1);
+          tc::tmem_st_u16(tmem + lane_base + EP(x, 2) + c0, e2);
+        } else {
+          tc::tmem_st_u8(tmem + lane_base + EP(x, 0) + c0, e0);
+          tc::tmem_st_u8(tmem + lane_base + EP(x, 1) + c0, e1);
+          tc::tmem_st_u8(tmem + lane_base + EP(x, 2) + c0, e2);
         }
-        if (ew == 0 && lane == 0) {
-          tc::tma_store_2d(&tmR, rb * 128, (int)(t * nu), sm + (size_t)s * a.ustage);
-          tc::bulk_wait_read_all();
-          mbar_arrive(bars + U_EMPTY + s);
-        }
+        tc::tmem_st_wait();
+        tc::fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bars + U_EREADY + x);
+        // The previous W group is added one tile into the next one (its
+        // products are done by then); the last groups at the unit's end.
         const int64_t rel = t - t0;
-        if (rel % kWGroup == kWGroup - 1 || t == t1 - 1) {
-          // the W group's total into the unit's rows (its first group starts them)
-          bool wgood = tc::wait(bars + U_WFULL, (uint32_t)(wgE & 1), err, tmo);
-          wgood = __all_sync(0xffffffffu, wgood);
-          if (!collective_ok(wgood)) {
-            ok = false;
-            break;
-          }
-          ++wgE;
-          tc::fence_after();
-          const int kh = KN / 2;
-          for (int k0 = 0; k0 < kh; k0 += 8) {
-            float w[8];
-            tc::tmem_ld<8>(tmem + lane_base + WACC + (uint32_t)(h * kh + k0), w);
-#pragma unroll
-            for (int v = 0; v < 8; ++v) {
-              float* q = wsum + (size_t)(h * kh + k0 + v) * 128 + row;
-              *q = rel < kWGroup ? w[v] : *q + w[v];
-            }
-          }
-          tc::fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(bars + U_WEMPTY);
-        }
+        if (rel % kWGroup == 0 && rel > 0) ok = drain_w(wgE == wg_first);
+        if (ok && t == t1 - 1)
+          while (ok && wgE < wg_first + ngroups(n)) ok = drain_w(wgE == wg_first);
       }
       if (!ok) break;
       // the unit's W rows: [u][k][128]
-      for (int k = h * (KN / 2); k < (h + 1) * (KN / 2); ++k)
+      for (int k = h * kh; k < (h + 1) * kh; ++k)
         a.Wp[((size_t)u * KN + (size_t)k) * 128 + row] = wsum[(size_t)k * 128 + row];
       if (ui + 1 < nunits_cta) {
         int rb2;
@@ -881,7 +988,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) update_kernel(UArgs a, const __
         load_y(rb2);
       }
     }
-    if (ew == 0 && lane == 0) tc::bulk_wait_all();
     acc2 = warp_sum_f64(acc2);
     if (lane == 0) red[ew] = acc2;
   }
@@ -1186,7 +1292,10 @@ cudaError_t batched_sweep(BatchedState* b, float* R, float* Y, float* C, int ld,
   ga.mchunks = P.mchunks;
   ga.N = N;
   ga.gtiles = P.gtiles;
-  ga.gstage = P.gstage;
+  ga.rs = P.grs;
+  ga.bs = P.gbs;
+  ga.rstage = P.grstage;
+  ga.bstage = P.gbstage;
   ga.timeout_ns = timeout_ns;
   g_kernel<<<P.ggrid, kTcThreads, P.gsmem, s>>>(ga, b->tmG);
   e = cudaGetLastError();
@@ -1229,10 +1338,12 @@ cudaError_t batched_sweep(BatchedState* b, float* R, float* Y, float* C, int ld,
   ua.RB = P.RB;
   ua.Q = P.Q;
   ua.units = P.units;
-  ua.stages = P.ustages;
+  ua.rs = P.urs;
+  ua.zs = P.uzs;
   ua.N = N;
   ua.utiles = P.utiles;
-  ua.ustage = P.ustage;
+  ua.rstage = P.urstage;
+  ua.zstage = P.uzstage;
   ua.timeout_ns = timeout_ns;
   if (P.nu == 64)
     update_kernel<64><<<P.ugrid, kTcThreads, P.usmem, s>>>(ua, b->tmU);
