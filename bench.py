@@ -220,6 +220,78 @@ def serve_bench(did, n_req, rate, precision, budget_gb=120.0, max_slots=64, roun
             "note": "saturated: offered work exceeds one GPU at this rate" if rate >= 50 else ""}
 
 
+def workload_run(did, name, precision, sweeps, warmup, stream, tol=0.0, max_sweeps=None):
+    """One context on a named workload (device-generated X, seed 0): warm-up
+    sweeps, then `sweeps` timed sweeps (or, with tol > 0, did_factor up to
+    max_sweeps under the relative-change rule).  Returns sweeps/s over the
+    timed region (CUDA events on the library's stream), the sweep kernel's
+    roofline on the bytes it moves, the refreshes, and f(B, C)."""
+    import torch
+    w = WORKLOADS[name]
+    M, N, K = w["M"], w["N"], w["K"]
+    prec = did.DID_BF16R if precision == "bf16r" else did.DID_FP32
+    s_bytes = 2 if prec == did.DID_BF16R else 4
+    X = torch.empty((N, M), dtype=torch.float32, device="cuda")
+    if w["gen"] == "image":
+        did.did_generate_image(X, M, N, 0, 0.8, stream=stream)
+    else:
+        did.did_generate_planted(X, M, N, K, 0, coords=w["coords"], zero_frac=w["zero_frac"], sigma=w["sigma"],
+                                 salt_frac=w["salt_frac"], salt_value=5.0, stream=stream)
+    c = did.Context(X, M, N, K, seed=0, precision=prec, refresh_every=w["refresh_every"],
+                    init_scale=w["init_scale"], stream=stream)
+    del X
+    for _ in range(warmup):
+        c.sweep(1)
+    i0 = c.info()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    if tol > 0:
+        done, _ = c.factor(max_sweeps, tol)
+    else:
+        c.sweep(sweeps)
+        done = sweeps
+    e1.record(stream)
+    torch.cuda.synchronize()
+    i1 = c.info()
+    ms = e0.elapsed_time(e1)
+    kms = i1["sweep_kernel_ms"] - i0["sweep_kernel_ms"]
+    passes = sweep_passes(K, i1["lazy_writeback"])
+    alg = done * float(passes) * M * N * s_bytes + (i1["prologue_launches"] - i0["prologue_launches"]) * M * N * s_bytes
+    peak, _ = measured_peaks()
+    f = c.objective()
+    trace = c.trace()
+    c.close()
+    return {"workload": name, "precision": precision, "sweeps": int(done), "warmup": warmup,
+            "value": done / (ms / 1000.0), "unit": "sweeps/s", "ms_per_sweep": ms / max(1, done),
+            "roofline_frac": alg / (kms / 1e3) / 1e9 / peak if kms > 0 else None,
+            "alg_bytes_per_sweep": float(passes) * M * N * s_bytes, "writeback": "deferred" if i1["lazy_writeback"] else "eager",
+            "refreshes": int(i1["refreshes"] - i0["refreshes"]),
+            "refresh_kind": ("tcgen05" if i1["tc_refreshes"] > i0["tc_refreshes"] else "SIMT") if i1["refreshes"] > i0["refreshes"] else None,
+            "objective_fBC": f, "trace_last": float(trace[-1]),
+            "gpu_launches": int((i1["sweep_launches"] - i0["sweep_launches"]) + (i1["dense_launches"] - i0["dense_launches"])
+                                + 3 * (i1["tc_refreshes"] - i0["tc_refreshes"]))}
+
+
+def precision_pair(did, name, sweeps, warmup, stream, tol=0.0, max_sweeps=None):
+    """FP32 and BF16-R on the same workload and seed: both throughputs, their
+    ratio, and how far apart the factorisations' objectives f(B, C) end."""
+    f32 = workload_run(did, name, "fp32", sweeps, warmup, stream, tol, max_sweeps)
+    # With a stopping rule the BF16-R arm runs the sweeps the float32 arm took:
+    # its monitored objective carries the residual's rounding (about 1e-5
+    # relative change per sweep), so the same rule would run it to max_sweeps.
+    b16 = workload_run(did, name, "bf16r", f32["sweeps"] if tol > 0 else sweeps, warmup, stream)
+    note = "same seed and start; the float32 line is the library's default for this shape (%s write-back)" % (
+        f32["writeback"])
+    if tol > 0:
+        note += "; float32 stops at relative change < %g (max %d sweeps), BF16-R runs the same sweep count" % (
+            tol, max_sweeps)
+    return {"workload": name, "fp32": f32, "bf16r": b16, "ratio_bf16r_vs_fp32": b16["value"] / f32["value"],
+            "objective_rel_diff": abs(b16["objective_fBC"] - f32["objective_fBC"]) / f32["objective_fBC"],
+            "note": note}
+
+
 def batched_flops(M, N, K):
     """Algorithmic float32 flops of one batched sweep of Algorithm 3 with a
     pending correction: g = B^T R (2KMN), R -= [D B][C_old; dl] (4KMN),
@@ -363,6 +435,11 @@ def main():
     ap.add_argument("--phases", action="store_true",
                     help="also report the per-k phase split of the last timed sweep (globaltimer stamps)")
     ap.add_argument("--no-bf16", action="store_true", help="skip the BF16-R measurement on the same workload")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the precision workload (10000x500000, K=100: FP32 vs BF16-R, 50 sweeps each) and "
+                         "the image-like workload (784x70000, K=16) lines")
+    ap.add_argument("--precision-sweeps", type=int, default=50,
+                    help="timed sweeps of each arm on the precision workload")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-requests", type=int, default=128,
                     help="requests of the serving stream to run (4096 in the full stream)")
@@ -560,6 +637,17 @@ def main():
     else:
         del X
 
+    workloads = None
+    if not args.no_workloads and not args.shape and args.order == "interleaved" and ws == 1:
+        # the configuration the BF16-R target is quoted on, and the MNIST-shaped one
+        workloads = {
+            "salt_10000x500000_k100": precision_pair(did, "salt_10000x500000_k100", args.precision_sweeps, 3,
+                                                     stream),
+            "image_like_784x70000_k16": precision_pair(did, "image_like_784x70000_k16", 0, 3, stream,
+                                                       tol=1e-5, max_sweeps=200),
+        }
+        other_launches += sum(v[a]["gpu_launches"] for v in workloads.values() for a in ("fp32", "bf16r"))
+
     serving = None
     if not args.no_serve and not args.shape:
         serving = [serve_bench(did, args.serve_requests, args.serve_rate, did.DID_FP32),
@@ -615,6 +703,7 @@ def main():
             "step_kernel_ms": step_ms,
             "refresh": refresh,
             "bf16r": bf16,
+            "workloads": workloads,
             "orders": orders,
             "serving": serving,
             "phases": phases,

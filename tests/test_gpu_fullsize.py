@@ -105,3 +105,54 @@ def test_image_like_784x70000_k16_fp32(did):
     X, st = generate(did, M, N, K, "image")
     a = run(did, X, M, N, K, st, 30, init_scale=True)
     check_properties(X, a, M, tol_r=2.0 ** -16, tol_fix=1e-5, tol_f=1e-5, label="fp32 784x70000x16")
+
+
+def check_batched(X, out, tol_r, tol_fix, tol_f, label):
+    """The batched order (C step, then B step): the last block of a sweep is
+    b_K, at its own closed form b_K = [b_K + R c_K^T / ||c_K||^2]_+ on sampled
+    rows of the true residual; R == X - B C on sampled columns; f(B, C) equals
+    the trace value; the trace does not rise."""
+    B = out["B"].astype(np.float64)
+    C = out["C"].astype(np.float64)
+    R = out["R"]
+    t = out["trace"]
+    rs = np.random.default_rng(1)
+    cols = np.sort(rs.choice(C.shape[1], 256, replace=False))
+    Xs = X[torch.as_tensor(cols, device=X.device)].cpu().numpy().astype(np.float64).T
+    Rs = R[:, cols].astype(np.float64)
+    scale = (np.abs(Xs) + np.abs(B) @ np.abs(C[:, cols])).max(axis=0, keepdims=True)
+    err_r = float(np.max(np.abs(Rs - (Xs - B @ C[:, cols])) / scale))
+    rows = np.sort(rs.choice(B.shape[0], 64, replace=False))
+    cK = C[-1]
+    cc = float(cK @ cK)
+    Rr = R[rows].astype(np.float64)                      # 64 full rows
+    bK = B[rows, -1]
+    bK_star = np.maximum(bK + (Rr @ cK) / cc, 0.0)
+    fix_scale = (np.abs(Rr) @ np.abs(cK)) / cc + np.abs(bK)
+    err_fix = float(np.max(np.abs(bK - bK_star) / (fix_scale + 1e-30)))
+    err_f = abs(out["f"] - t[-1]) / t[-1]
+    rises = np.diff(t) / t[:-1]
+    print("%s: trace %.6g -> %.6g, max rise %.3g, R err %.3g, b_K fixed-point err %.3g, f vs trace %.3g"
+          % (label, t[0], t[-1], rises.max(), err_r, err_fix, err_f))
+    assert rises.max() <= 1e-6
+    assert err_r <= tol_r
+    assert err_fix <= tol_fix
+    assert err_f <= tol_f
+    assert B.min() >= 0 and C.min() >= 0
+
+
+def test_planted_exp_5000x200000_k50_batched(did):
+    """The batched order at the size and cadence its benchmark line runs."""
+    M, N, K = 5000, 200000, 50
+    X, st = generate(did, M, N, K, "planted_exp")
+    a = run(did, X, M, N, K, st, 12, refresh_every=10, order=did.DID_ORDER_DID_BATCHED)
+    check_batched(X, a, tol_r=2.0 ** -16, tol_fix=1e-5, tol_f=1e-5, label="batched 5000x200000x50")
+    b = run(did, X, M, N, K, st, 12, refresh_every=10, order=did.DID_ORDER_DID_BATCHED)
+    assert np.array_equal(a["B"], b["B"]) and np.array_equal(a["C"], b["C"])
+
+
+def test_image_like_784x70000_k16_batched(did):
+    M, N, K = 784, 70000, 16
+    X, st = generate(did, M, N, K, "image")
+    a = run(did, X, M, N, K, st, 30, init_scale=True, order=did.DID_ORDER_DID_BATCHED)
+    check_batched(X, a, tol_r=2.0 ** -16, tol_fix=1e-5, tol_f=1e-5, label="batched 784x70000x16")

@@ -112,6 +112,31 @@ def test_stopping_rule_and_bf16(did):
         assert abs(r["iters"] - 99) <= (1 if prec == did.DID_FP32 else 5)
 
 
+def test_bf16r_served_result(did):
+    """A request served with a bfloat16 residual: the factorisation it returns
+    reaches f(B, C) (evaluated in float64 on the host from the returned factors)
+    within 1e-3 of the same request served in float32, and of the oracle."""
+    M, N, K, seed, it = 500, 6000, 12, 88, 20
+    out = {}
+    for prec in (did.DID_FP32, did.DID_BF16R):
+        with did.Server(4 * GB, precision=prec, max_slots=4, round_sweeps=4) as srv:
+            t = srv.submit(M, N, K, seed, max_iter=it, tol=0.0)
+            r = srv.wait(t)
+            assert r["status"] == did.DID_OK and r["iters"] == it
+            out[prec] = srv.fetch(t)
+    X, _, _ = W.planted(M, N, K, seed, sigma=0.01)      # the serving recipe, on the host
+    B0, C0 = W.init_factors(M, N, K, seed)
+    ref = O.factor(X, B0, C0, order="hals", max_iter=it, stop="none")
+    f = {p: O.objective(X, np.asarray(b, np.float64), np.asarray(c, np.float64)) for p, (b, c) in out.items()}
+    f_ref = ref["trace"][-1]
+    d32 = abs(f[did.DID_BF16R] - f[did.DID_FP32]) / f[did.DID_FP32]
+    dref = abs(f[did.DID_BF16R] - f_ref) / f_ref
+    print("served f(B,C): fp32 %.9g, bf16r %.9g, oracle %.9g: bf16r vs fp32 %.3g, vs oracle %.3g"
+          % (f[did.DID_FP32], f[did.DID_BF16R], f_ref, d32, dref))
+    assert d32 <= 1e-3 and dref <= 1e-3
+    assert abs(f[did.DID_FP32] - f_ref) / f_ref <= 1e-5
+
+
 def test_oversize_rejected(did):
     with did.Server(1 * GB, max_slots=4) as srv:
         with pytest.raises(did.DIDError) as e:
