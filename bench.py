@@ -557,7 +557,7 @@ def main():
     if nref:
         rms = (info1["dense_kernel_ms"] - info0["dense_kernel_ms"] + info1["tc_refresh_ms"] - info0["tc_refresh_ms"]) / nref
         rbytes = M * N * (4 + s_bytes)
-        kind = ("tcgen05 BF16x3" if prec == did.DID_BF16R else "tcgen05 TF32x3") if tc_launches else "SIMT FP32"
+        kind = ("tcgen05 BF16x3" if prec == did.DID_BF16R else "tcgen05 BF16x6") if tc_launches else "SIMT FP32"
         refresh = {"kind": kind, "launches": int(nref),
                    "ms_per_refresh": rms, "alg_bytes": rbytes, "GBps": rbytes / (rms / 1e3) / 1e9,
                    "tflops": 2.0 * M * N * K * (3 if tc_launches else 1) / (rms / 1e3) / 1e12}

@@ -66,9 +66,10 @@ typedef enum { DID_FP32 = 0, DID_BF16R = 1 } did_precision;
  *   (v_ik/v_ii) delta b_k]_+; the delta b correction of R is applied lazily
  *   by the next sweep.  Float32 residual only, K <= 64 (did_create_ex
  *   returns DID_EINVAL otherwise).  The products run on the tensor cores as
- *   TF32x3 (each float32 operand split into a TF32 part and a remainder,
- *   three products accumulated in float32), in two passes over R per sweep:
- *   one forms g, one applies the rank-2K update and forms W.  The objective
+ *   BF16x6 (each float32 operand split into three bfloat16 terms, the six
+ *   leading products accumulated in float32: float32 accuracy), in two
+ *   passes over R per sweep: one reads R and forms g, one reads and writes R
+ *   (the rank-2K update) and forms W.  The objective
  *   of each sweep is the float64 norm of the residual after the C step, with
  *   the B step's change taken from an exact float64 identity in W, V and
  *   delta b. */
@@ -108,7 +109,7 @@ typedef struct {
  * did_get_phase_times; costs four 8-byte stores per k. */
 #define DID_FLAG_PHASE_TIMES 1
 /* did_options.flags: refresh R = X - B C with the float32 SIMT pass instead of
- * the tensor-core pass (BF16x3 for a bfloat16 residual with K <= 128, TF32x3
+ * the tensor-core pass (BF16x3 for a bfloat16 residual with K <= 128, BF16x6
  * for a float32 one with K <= 64; larger K always takes the SIMT pass). */
 #define DID_FLAG_SIMT_REFRESH 2
 /* did_options.flags (DID_ORDER_INTERLEAVED): deferred write-back defers the
@@ -227,12 +228,13 @@ did_status did_objective(did_ctx* ctx, double* obj);
 did_status did_residual_objective(did_ctx* ctx, double* obj);
 
 /* Recompute R = X - B C densely (Algorithm 3 recomputes e_j := x_j - B c_j)
- * on the tensor cores (tcgen05, three products Bh Ch + Bh Cl + Bl Ch of split
- * operands with float32 accumulation): bfloat16 halves for a BF16 residual
- * with K <= 128, TF32 parts for an FP32 residual with K <= 64.  Larger K or
- * DID_FLAG_SIMT_REFRESH: the float32 SIMT pass.  Returns DID_ETIMEOUT if a
- * bounded device wait of the tensor-core pass ran out (R is then recomputed
- * before the next sweep). */
+ * on the tensor cores (tcgen05, bfloat16 products with float32
+ * accumulation): for an FP32 residual with K <= 64 each operand is split into
+ * three bfloat16 terms and the six leading products are summed (BF16x6,
+ * float32 accuracy); for a BF16 residual with K <= 128 two terms and three
+ * products (BF16x3).  Larger K or DID_FLAG_SIMT_REFRESH: the float32 SIMT
+ * pass.  Returns DID_ETIMEOUT if a bounded device wait of the tensor-core
+ * pass ran out (R is then recomputed before the next sweep). */
 did_status did_refresh_residual(did_ctx* ctx);
 
 /* Copy the factors B (M x K column-major) and C (K x N row-major) of

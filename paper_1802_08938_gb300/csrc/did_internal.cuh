@@ -357,7 +357,7 @@ int dense_grid();
 cudaError_t launch_dense(const DenseArgs& a, cudaStream_t s);
 
 // Tensor-core refresh R = X - B C: BF16x3 products for a bfloat16 residual
-// (K <= 128), TF32x3 for a float32 one (f32, K <= 64).  With P1 non-null it
+// (K <= 128), BF16x6 for a float32 one (f32, K <= 64).  With P1 non-null it
 // also writes the partials of R c_1^T (2 refresh_tc_grid() rows of ld floats,
 // row 2 cta + column half) and of ||c_1||^2 (CC1, as many doubles), in the
 // layout the sweep's first b-reduce takes through SweepArgs::npart_first.

@@ -3,23 +3,26 @@
 // Algorithm 3 recomputes the residual e_j := x_j - B c_j at the top of every
 // iteration; the sweep keeps R and updates it in place, so a periodic dense
 // refresh resets the drift of its roundings.  The product B C is a rank-K
-// contraction, done as three products of split operands with float32
-// accumulation.  With B = Bh + Bl and C = Ch + Cl, B C ~= Bh Ch + Bh Cl + Bl Ch:
-//   bfloat16 residual ("BF16x3", kind::f16, K <= 128): bfloat16 halves; the
-//     dropped Bl Cl term is ~2^-16 relative, far below the bfloat16 rounding of
-//     the stored R;
-//   float32 residual ("TF32x3", kind::tf32, K <= 64): Bh is the operand
-//     rounded to TF32's 11 significand bits, Bl = B - Bh (exact in float32,
-//     read by the tensor core as TF32); the error is ~2^-21 relative to
-//     |B||C| per product, of either sign.
+// contraction on the bfloat16 tensor cores (kind::f16, float32 accumulation)
+// of split operands, each float32 operand a sum of bfloat16 terms:
+//   float32 residual ("BF16x6", K <= 64): three terms per operand
+//     (tc::split_bf16x3) and the six products whose terms reach 2^-18 of the
+//     leading one, which matches float32 arithmetic;
+//   bfloat16 residual ("BF16x3", K <= 128): two terms per operand and three
+//     products; the dropped terms are ~2^-16 relative, far below the bfloat16
+//     rounding of the stored R.
 //
 // Kernel structure (one CTA per SM, persistent over 64-column tiles):
 //   warp 0      producer: TMA bulk copies of the C-factor tile (once per
 //               column tile) and the B-factor row block (from L2; double
-//               buffered, so the next block loads while the MMAs run), and
-//               one 2-D tensor copy of the 128 x 64 X tile (double buffered);
+//               buffered, so the next block loads while the MMAs run);
+//   warp 3      producer of the 128 x 64 X tiles (one 2-D tensor copy each)
+//               into a ring of as many buffers as shared memory holds (2-4),
+//               so the X reads run ahead of the epilogue;
 //   warp 1      allocates 128 TMEM columns (two 128 x 64 float32 accumulators)
 //               and one elected thread issues the tcgen05.mma instructions;
+//   warp 2      stores each finished tile of R by one 2-D tensor copy and
+//               releases its X buffer once the copy has read it;
 //   warps 4-11  epilogue, two warps per TMEM lane quarter (warp w reads lanes
 //               32 (w % 4).. and columns 32 ((w - 4) / 4)..): tcgen05.ld of the
 //               accumulator, R = X - D (rounded to bfloat16 for that mode)
@@ -32,10 +35,10 @@
 //               needs no extra read of R after a refresh.
 // Operands live in global memory pre-split and pre-tiled in the no-swizzle
 // K-major core-matrix layout (8 rows x 16 bytes per core matrix, core matrices
-// along K 128 bytes apart, along M/N Kp*E*8 bytes apart for E-byte elements),
-// so each operand tile is one contiguous bulk copy and its shared-memory
-// descriptor is a plain (start, LBO = 128, SBO = Kp*E*8) triple.  One MMA
-// consumes 32 bytes of K (16 bfloat16 or 8 TF32 elements).
+// along K 128 bytes apart, along M/N Kp*16 bytes apart for bfloat16), so each
+// operand tile is one contiguous bulk copy and its shared-memory descriptor
+// is a plain (start, LBO = 128, SBO = Kp*16) triple.  One MMA consumes 16
+// bfloat16 elements of K (32 bytes).
 //
 // Every mbarrier wait is bounded; on expiry the kernel records the error,
 // stops issuing work, waits (bounded) for its copies and MMAs, frees its
@@ -52,38 +55,40 @@ constexpr int kTcThreads = 384;     // 12 warps: producer, MMA, two idle, eight 
 constexpr int kEpiWarps = 8;
 constexpr int kTileM = 128;         // rows per MMA (TMEM lanes)
 constexpr int kTileN = 64;          // columns per tile (MMA N)
-constexpr int kMaxKp = 128;         // K padded to a multiple of 16, at most 128 (bfloat16)
-constexpr int kMaxKpTf32 = 64;      // TF32 operands take twice the shared memory
+constexpr int kMaxKp = 128;         // K padded to a multiple of 16, at most 128 (bfloat16 residual)
+constexpr int kMaxKpF32 = 64;       // three-term operands take 1.5x the shared memory
+constexpr int kMaxXBuf = 4;         // X tile ring
 constexpr int kTmemCols = 128;      // two accumulators of kTileN columns
 
 struct TcArgs {
   const float* X;            // ld x N float32, column-major
   void* R;                   // ld x N output (bfloat16 or float32)
-  const void* Ahl;           // [row blocks][2][128 rows x Kp] tiled B factor (hi, lo)
-  const void* Bhl;           // [col tiles][2][64 cols x Kp] tiled C factor (hi, lo)
+  const void* Ahl;           // [row blocks][terms][128 rows x Kp] tiled B factor
+  const void* Bhl;           // [col tiles][terms][64 cols x Kp] tiled C factor
   double* part;              // [grid] sum of R^2 per CTA
   const float* c1;           // row 1 of C (N floats), or null: no partials
   float* P1;                 // [2 grid][ld] partials of R c_1^T (row 2 cta + column half)
   double* CC1;               // [2 grid] partials of ||c_1||^2
   int* err;                  // error word
   int M, ld, Kp;
+  int xbufs;                 // X tile buffers (2..kMaxXBuf)
   int64_t N;
   int row_blocks;            // ceil(ld / 128)
   int64_t col_tiles;         // ceil(N / 64)
   uint64_t timeout_ns;
 };
 
-// Shared memory plan (bytes).
+// Shared memory plan (bytes) for NT-term bfloat16 operands and XB X buffers.
 struct TcSmem {
   size_t A, B, X, bars, tmem_slot, red, steps, total;
 };
-__host__ __device__ __forceinline__ TcSmem tc_smem(int Kp, int E) {
+__host__ __device__ __forceinline__ TcSmem tc_smem(int Kp, int NT, int XB) {
   TcSmem L;
   size_t o = 0;
-  L.A = o;    o += (size_t)2 * 2 * kTileM * Kp * E;      // two buffers of the Bh, Bl row block
-  L.B = o;    o += (size_t)2 * kTileN * Kp * E;          // Ch, Cl column tile
-  L.X = o;    o += (size_t)2 * kTileN * kTileM * 4;      // two X tiles [64 cols][128 rows]
-  L.bars = o; o += 16 * sizeof(uint64_t);
+  L.A = o;    o += (size_t)2 * NT * kTileM * Kp * 2;     // two buffers of the B-factor row block
+  L.B = o;    o += (size_t)NT * kTileN * Kp * 2;         // the C-factor column tile
+  L.X = o;    o += (size_t)XB * kTileN * kTileM * 4;     // X tiles [64 cols][128 rows]
+  L.bars = o; o += 24 * sizeof(uint64_t);
   L.tmem_slot = o; o += 16;
   L.red = o;  o += 8 * sizeof(double);
   L.steps = o; o += 16;
@@ -96,21 +101,24 @@ enum {
   BAR_B_FULL = 0,     // C-factor tile landed
   BAR_A_FULL = 1,     // 1, 2: B-factor row block buffers landed
   BAR_A_EMPTY = 3,    // 3, 4: MMAs of a step done reading its A buffer (and B)
-  BAR_X_FULL = 5,     // 5, 6: X tile buffers landed
-  BAR_X_EMPTY = 7,    // 7, 8: the R tile stored from an X buffer has been read out
-  BAR_ACC_FULL = 9,   // 9, 10: accumulator ready (tcgen05.commit)
-  BAR_ACC_EMPTY = 11, // 11, 12: epilogue done reading an accumulator (one arrival per epilogue warp)
-  BAR_COUNT = 13
+  BAR_ACC_FULL = 5,   // 5, 6: accumulator ready (tcgen05.commit)
+  BAR_ACC_EMPTY = 7,  // 7, 8: epilogue done reading an accumulator (one arrival per epilogue warp)
+  BAR_X_FULL = 9,     // 9..12: X tile buffers landed
+  BAR_X_EMPTY = 13,   // 13..16: the R tile stored from an X buffer has been read out
+  BAR_EPI_DONE = 17,  // 17..20: a tile of R is complete in an X buffer (one arrival per epilogue warp)
+  BAR_COUNT = 21
 };
 
-// F32: TF32x3 operands and a float32 residual; otherwise BF16x3 and bfloat16.
+// F32: a float32 residual from BF16x6 products; otherwise a bfloat16 residual from BF16x3.
 template <bool F32>
 __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a, const __grid_constant__ CUtensorMap tmX,
                                                                   const __grid_constant__ CUtensorMap tmR) {
-  constexpr int E = F32 ? 4 : 2;                  // operand element bytes
-  constexpr int KSTEP = F32 ? 8 : 16;             // K per MMA (32 bytes)
+  constexpr int NT = F32 ? 3 : 2;                 // bfloat16 terms per operand
+  constexpr int NPROD = F32 ? 6 : 3;              // products p_i q_j with i + j <= NT - 1
+  constexpr int KSTEP = 16;                       // K per MMA (32 bytes)
   extern __shared__ __align__(1024) unsigned char sm[];
-  const TcSmem L = tc_smem(a.Kp, E);
+  const int XB = a.xbufs;
+  const TcSmem L = tc_smem(a.Kp, NT, XB);
   unsigned char* sA = sm + L.A;
   unsigned char* sB = sm + L.B;
   float* sX = reinterpret_cast<float*>(sm + L.X);
@@ -121,16 +129,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a, con
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int Kp = a.Kp;
-  const uint32_t a_bytes = 2u * kTileM * Kp * E;
-  const uint32_t b_bytes = 2u * kTileN * Kp * E;
-  const uint32_t a_split = (uint32_t)kTileM * Kp * E;     // bytes of one split of the A tile
-  const uint32_t b_split = (uint32_t)kTileN * Kp * E;
+  const uint32_t a_bytes = (uint32_t)NT * kTileM * Kp * 2;
+  const uint32_t b_bytes = (uint32_t)NT * kTileN * Kp * 2;
+  const uint32_t a_split = (uint32_t)kTileM * Kp * 2;     // bytes of one term of the A tile
+  const uint32_t b_split = (uint32_t)kTileN * Kp * 2;
 
   if (threadIdx.x == 0) {
     mma_steps[0] = 0;
     mma_steps[1] = 0;     // epilogue failure flag
     for (int i = 0; i < BAR_COUNT; ++i) {
-      const bool per_warp = i == BAR_ACC_EMPTY || i == BAR_ACC_EMPTY + 1;
+      const bool per_warp =
+          i == BAR_ACC_EMPTY || i == BAR_ACC_EMPTY + 1 || (i >= BAR_EPI_DONE && i < BAR_EPI_DONE + kMaxXBuf);
       mbar_init(bars + i, per_warp ? kEpiWarps : 1);
     }
   }
@@ -155,7 +164,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a, con
         const int64_t ti = s / a.row_blocks;
         const int rb = (int)(s % a.row_blocks);
         const int64_t tile = blockIdx.x + ti * gridDim.x;
-        const int64_t j0 = tile * kTileN;
         // A_EMPTY + (t & 1) completes once per use of buffer t & 1: for step t
         // its phase parity is (t >> 1) & 1.
         if (rb == 0 && s > 0) {
@@ -173,25 +181,33 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a, con
         mbar_arrive_expect_tx(bars + BAR_A_FULL + abuf, a_bytes);
         bulk_load(sA + (size_t)abuf * a_bytes, reinterpret_cast<const unsigned char*>(a.Ahl) + (size_t)rb * a_bytes,
                   a_bytes, bars + BAR_A_FULL + abuf);
-        // X tile: one 2-D tensor copy of rows rb*128.., columns j0.. into
-        // buffer s & 1 (element (row, c) at c*128 + row; rows past ld and
-        // columns past N are filled with zeros and count in the bytes)
-        const int xb = (int)(s & 1);
-        if (s >= 2 && !tc::wait(bars + BAR_X_EMPTY + xb, (uint32_t)(((s - 2) >> 1) & 1), err, tmo)) break;
-        mbar_arrive_expect_tx(bars + BAR_X_FULL + xb, (uint32_t)(kTileM * kTileN * 4));
-        asm volatile(
-            "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-            "[%4];" ::"r"(smem_u32(sX + (size_t)xb * kTileN * kTileM)),
-            "l"(reinterpret_cast<uint64_t>(&tmX)), "r"(rb * kTileM), "r"((int)j0), "r"(smem_u32(bars + BAR_X_FULL + xb))
-            : "memory");
       }
+    }
+  } else if (warp == 3) {
+    // ---------------------------------------------------------- X producer
+    // X tile of step s: one 2-D tensor copy of rows rb*128.., columns j0..
+    // into buffer s % XB (element (row, c) at c*128 + row; rows past ld and
+    // columns past N are filled with zeros and count in the bytes)
+    if (lane == 0) {
+      int64_t s = 0;
+      for (; s < nsteps; ++s) {
+        const int64_t ti = s / a.row_blocks;
+        const int rb = (int)(s % a.row_blocks);
+        const int64_t j0 = (blockIdx.x + ti * gridDim.x) * kTileN;
+        const int xb = (int)(s % XB);
+        if (s >= XB && !tc::wait(bars + BAR_X_EMPTY + xb, (uint32_t)(((s / XB) - 1) & 1), err, tmo)) break;
+        mbar_arrive_expect_tx(bars + BAR_X_FULL + xb, (uint32_t)(kTileM * kTileN * 4));
+        tc::tma_load_2d(sX + (size_t)xb * kTileN * kTileM, &tmX, rb * kTileM, (int)j0, bars + BAR_X_FULL + xb);
+      }
+      for (int64_t d = s > XB ? s - XB : 0; d < s; ++d)
+        mbar_wait_bounded(bars + BAR_X_FULL + (d % XB), (uint32_t)((d / XB) & 1), err, tmo);
     }
   } else if (warp == 1) {
     // ----------------------------------------------------------- MMA issue
     if (lane == 0) {
-      const uint32_t idesc = F32 ? tc::instr_desc_tf32(kTileM, kTileN) : tc::instr_desc_bf16(kTileM, kTileN);
+      const uint32_t idesc = tc::instr_desc_bf16(kTileM, kTileN);
       const uint32_t sA0 = smem_u32(sA), sB0 = smem_u32(sB);
-      const uint32_t sbo = (uint32_t)Kp * E * 8;   // next 8-row group
+      const uint32_t sbo = (uint32_t)Kp * 16;      // next 8-row group
       for (int64_t s = 0; s < nsteps; ++s) {
         const int rb = (int)(s % a.row_blocks);
         const int64_t ti = s / a.row_blocks;
@@ -201,25 +217,40 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a, con
         if (s >= 2 && !tc::wait(bars + BAR_ACC_EMPTY + ab, (uint32_t)(((s - 2) >> 1) & 1), err, tmo)) break;
         tc::fence_after();
         const uint32_t d = tmem + (uint32_t)(ab * kTileN);
-        uint32_t acc = 0;
-        // Bh Ch, Bh Cl, Bl Ch
-        for (int prod = 0; prod < 3; ++prod) {
-          const uint32_t aoff = prod == 2 ? a_split : 0u;
-          const uint32_t boff = prod == 1 ? b_split : 0u;
+        // the NPROD products of the terms, p_i q_j with i + j < NT
+#pragma unroll
+        for (int pr = 0; pr < NPROD; ++pr) {
+          const int ti_a = pr == 2 || pr == 4 ? 1 : (pr == 5 ? 2 : 0);
+          const int ti_b = pr == 1 || pr == 4 ? 1 : (pr == 3 ? 2 : 0);
+          const uint32_t aoff = (uint32_t)ti_a * a_split;
+          const uint32_t boff = (uint32_t)ti_b * b_split;
           for (int kk = 0; kk < Kp / KSTEP; ++kk) {
             const uint64_t ad = tc::smem_desc(sA0 + (uint32_t)ab * a_bytes + aoff + (uint32_t)kk * 256u, 128u, sbo);
             const uint64_t bd = tc::smem_desc(sB0 + boff + (uint32_t)kk * 256u, 128u, sbo);
-            if (F32)
-              tc::mma_tf32(d, ad, bd, idesc, acc);
-            else
-              tc::mma_bf16(d, ad, bd, idesc, acc);
-            acc = 1;
+            tc::mma_bf16(d, ad, bd, idesc, (pr > 0 || kk > 0) ? 1u : 0u);
           }
         }
         tc::mma_commit(bars + BAR_ACC_FULL + ab);
         tc::mma_commit(bars + BAR_A_EMPTY + ab);
         *mma_steps = (int)(s + 1);
       }
+    }
+  } else if (warp == 2) {
+    // ------------------------------------------------------------ store warp
+    // Each finished tile of R leaves by one 2-D tensor store; its X buffer is
+    // released once the store has read it.
+    if (lane == 0) {
+      for (int64_t s = 0; s < nsteps; ++s) {
+        const int64_t ti = s / a.row_blocks;
+        const int rb = (int)(s % a.row_blocks);
+        const int64_t j0 = (blockIdx.x + ti * gridDim.x) * kTileN;
+        const int xb = (int)(s % XB);
+        if (!tc::wait(bars + BAR_EPI_DONE + xb, (uint32_t)((s / XB) & 1), err, tmo)) break;
+        tc::tma_store_2d(&tmR, rb * kTileM, (int)j0, sX + (size_t)xb * kTileN * kTileM);
+        tc::bulk_wait_read_all();
+        mbar_arrive(bars + BAR_X_EMPTY + xb);
+      }
+      tc::bulk_wait_all();
     }
   } else if (warp >= 4) {
     // ------------------------------------------------------------- epilogue
@@ -246,7 +277,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a, con
       const int rb = (int)(s % a.row_blocks);
       const int64_t tile = blockIdx.x + ti * gridDim.x;
       const int64_t j0 = tile * kTileN;
-      const int ab = (int)(s & 1), xb = (int)(s & 1);
+      const int ab = (int)(s & 1), xb = (int)(s % XB);
       const int i = rb * kTileM + row_in;
       const int ncol = (a.N - j0 < kTileN ? (int)(a.N - j0) : kTileN) - c0;
       // Loads for the partials go out before the waits: this row's running
@@ -258,7 +289,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a, con
         if (lane < ncol) cv = __ldg(a.c1 + j0 + c0 + lane);
       }
       ok = tc::wait(bars + BAR_ACC_FULL + ab, (uint32_t)((s >> 1) & 1), err, tmo) &&
-           tc::wait(bars + BAR_X_FULL + xb, (uint32_t)((s >> 1) & 1), err, tmo);
+           tc::wait(bars + BAR_X_FULL + xb, (uint32_t)((s / XB) & 1), err, tmo);
       // the warp-wide tcgen05.ld below needs every lane, so the lanes agree
       ok = __all_sync(0xffffffffu, ok);
       tc::fence_after();
@@ -291,29 +322,27 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a, con
         if (quarter == 0 && rb == 0) cc1 += (double)cv * (double)cv;
       }
       acc2 += (double)s2;
-      // Every epilogue warp has read its X values: the buffer now takes the
-      // tile of R (float32 in place, or bfloat16 packed at its start), which
-      // goes to global memory by one tensor store.  The warps decide
-      // together whether to go on, so none is left at a named barrier.
-      if (!collective_ok(ok)) break;
+      // The X buffer now takes the tile of R, which the store warp sends to
+      // global memory by one tensor store: float32 in place (each thread
+      // overwrites only the values it read), bfloat16 packed at the buffer's
+      // start, which overlaps X values of other warps, so for it the warps
+      // first agree that every X value has been read (and whether to go on:
+      // none is left at a named barrier).
       if (F32) {
+        if (!ok) break;
 #pragma unroll
         for (int c = 0; c < kTileN / 2; ++c) xs[c * kTileM] = d[c];
       } else {
+        if (!collective_ok(ok)) break;
         __nv_bfloat16* rs = reinterpret_cast<__nv_bfloat16*>(sX + (size_t)xb * kTileN * kTileM) +
                             (size_t)c0 * kTileM + row_in;
 #pragma unroll
         for (int c = 0; c < kTileN / 2; ++c) rs[c * kTileM] = __float2bfloat16_rn(d[c]);
       }
       fence_proxy_async_shared();
-      named_bar(3, kEpiWarps * 32);
-      if (ew == 0 && lane == 0) {
-        tc::tma_store_2d(&tmR, rb * kTileM, (int)j0, sX + (size_t)xb * kTileN * kTileM);
-        tc::bulk_wait_read_all();
-        mbar_arrive(bars + BAR_X_EMPTY + xb);
-      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bars + BAR_EPI_DONE + xb);
     }
-    if (ew == 0 && lane == 0) tc::bulk_wait_all();
     // A CTA without tiles still owns its partial rows: they are zero.
     if (prow && ntile_cta == 0)
       for (int rb = 0; rb < a.row_blocks; ++rb)
@@ -347,41 +376,27 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a, con
 }
 
 // ------------------------------------------------------------ operand prep
-// Tiled no-swizzle K-major layout of one split of a tile of `rows` rows, for
-// E-byte elements: element (r, k) at byte
-//   ((r/8) * (Kp*E/16) + (k*E)/16) * 128 + (r%8) * 16 + (k*E) % 16.
-template <int E>
+// Tiled no-swizzle K-major layout of one term of a bfloat16 tile: element
+// (r, k) at ((r/8) * (Kp/8) + k/8) * 64 + (r%8) * 8 + k%8.
 __device__ __forceinline__ size_t tiled_index(int r, int k, int Kp) {
-  constexpr int per16 = 16 / E;                  // elements per 16-byte core-matrix row
-  return ((size_t)(r >> 3) * (Kp / per16) + (k / per16)) * (8 * per16) + (r & 7) * per16 + (k % per16);
+  return ((size_t)(r >> 3) * (Kp >> 3) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7);
 }
 
-// Split of v into a high part and a remainder: bfloat16 halves (round to
-// nearest), or for TF32 the value rounded to its top 11 significand bits
-// (nearest, ties away from zero: add half a TF32 ulp to the magnitude bits,
-// clear the 13 low bits; a carry into the exponent is the correct rounding)
-// and the exact float32 remainder, signed and at most half a TF32 ulp.
-// Truncating instead would bias every remainder towards the operand's sign.
-template <typename T>
-struct Split;
-template <>
-struct Split<__nv_bfloat16> {
-  static __device__ __forceinline__ void run(float v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
-    hi = __float2bfloat16_rn(v);
-    lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+// NT bfloat16 terms of v: three (tc::split_bf16x3) for a float32 residual,
+// two (the value and its remainder, each rounded to nearest) for a bfloat16 one.
+template <int NT>
+__device__ __forceinline__ void split_terms(float v, __nv_bfloat16* t) {
+  if (NT == 3) {
+    tc::split_bf16x3(v, t[0], t[1], t[2]);
+  } else {
+    t[0] = __float2bfloat16_rn(v);
+    t[1] = __float2bfloat16_rn(v - __bfloat162float(t[0]));
   }
-};
-template <>
-struct Split<float> {
-  static __device__ __forceinline__ void run(float v, float& hi, float& lo) {
-    hi = __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xFFFFE000u);
-    lo = v - hi;
-  }
-};
+}
 
-// B factor (ld x K column-major float32) -> [row block][split][128 x Kp].
-template <typename T>
-__global__ void prep_b_kernel(const float* B, int M, int ld, int K, int Kp, int row_blocks, T* out) {
+// B factor (ld x K column-major float32) -> [row block][term][128 x Kp].
+template <int NT>
+__global__ void prep_b_kernel(const float* B, int M, int ld, int K, int Kp, int row_blocks, __nv_bfloat16* out) {
   const int64_t n = (int64_t)row_blocks * kTileM * Kp;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
        idx += (int64_t)gridDim.x * blockDim.x) {
@@ -389,17 +404,17 @@ __global__ void prep_b_kernel(const float* B, int M, int ld, int K, int Kp, int 
     const int64_t rg = idx / Kp;                 // global row
     const int rb = (int)(rg / kTileM), r = (int)(rg % kTileM);
     const float v = (rg < M && k < K) ? B[(size_t)k * ld + rg] : 0.f;
-    T hi, lo;
-    Split<T>::run(v, hi, lo);
-    T* base = out + (size_t)rb * 2 * kTileM * Kp;
-    base[tiled_index<sizeof(T)>(r, k, Kp)] = hi;
-    base[(size_t)kTileM * Kp + tiled_index<sizeof(T)>(r, k, Kp)] = lo;
+    __nv_bfloat16 t[NT];
+    split_terms<NT>(v, t);
+    __nv_bfloat16* base = out + (size_t)rb * NT * kTileM * Kp;
+#pragma unroll
+    for (int p = 0; p < NT; ++p) base[(size_t)p * kTileM * Kp + tiled_index(r, k, Kp)] = t[p];
   }
 }
 
-// C factor (K x N row-major float32) -> [column tile][split][64 x Kp].
-template <typename T>
-__global__ void prep_c_kernel(const float* C, int64_t N, int K, int Kp, int64_t col_tiles, T* out) {
+// C factor (K x N row-major float32) -> [column tile][term][64 x Kp].
+template <int NT>
+__global__ void prep_c_kernel(const float* C, int64_t N, int K, int Kp, int64_t col_tiles, __nv_bfloat16* out) {
   const int64_t n = col_tiles * kTileN * Kp;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
        idx += (int64_t)gridDim.x * blockDim.x) {
@@ -408,11 +423,11 @@ __global__ void prep_c_kernel(const float* C, int64_t N, int K, int Kp, int64_t 
     const int64_t ct = cg / kTileN;
     const int c = (int)(cg % kTileN);
     const float v = (cg < N && k < K) ? C[(size_t)k * N + cg] : 0.f;
-    T hi, lo;
-    Split<T>::run(v, hi, lo);
-    T* base = out + (size_t)ct * 2 * kTileN * Kp;
-    base[tiled_index<sizeof(T)>(c, k, Kp)] = hi;
-    base[(size_t)kTileN * Kp + tiled_index<sizeof(T)>(c, k, Kp)] = lo;
+    __nv_bfloat16 t[NT];
+    split_terms<NT>(v, t);
+    __nv_bfloat16* base = out + (size_t)ct * NT * kTileN * Kp;
+#pragma unroll
+    for (int p = 0; p < NT; ++p) base[(size_t)p * kTileN * Kp + tiled_index(c, k, Kp)] = t[p];
   }
 }
 
@@ -425,31 +440,32 @@ int sm_count_tc() {
 
 }  // namespace
 
-bool refresh_tc_supported(int K, bool f32) { return K >= 1 && K <= (f32 ? kMaxKpTf32 : kMaxKp); }
+bool refresh_tc_supported(int K, bool f32) { return K >= 1 && K <= (f32 ? kMaxKpF32 : kMaxKp); }
 
 size_t refresh_tc_workspace_bytes(int M, int ld, int64_t N, int K, bool f32) {
   const int Kp = (K + 15) / 16 * 16;
-  const int E = f32 ? 4 : 2;
+  const int NT = f32 ? 3 : 2;
   const int row_blocks = (ld + kTileM - 1) / kTileM;
   const int64_t col_tiles = (N + kTileN - 1) / kTileN;
   (void)M;
-  return (size_t)row_blocks * 2 * kTileM * Kp * E + (size_t)col_tiles * 2 * kTileN * Kp * E;
+  return ((size_t)row_blocks * kTileM + (size_t)col_tiles * kTileN) * NT * Kp * 2;
 }
 
 int refresh_tc_grid() { return sm_count_tc(); }
 
-template <typename T, bool F32>
+template <bool F32>
 static cudaError_t launch_tc(const float* X, void* R, const float* B, const float* C, int M, int ld, int64_t N,
                              int K, void* workspace, double* part, float* P1, double* CC1, int* err,
                              uint64_t timeout_ns, cudaStream_t s) {
   const int Kp = (K + 15) / 16 * 16;
   const int row_blocks = (ld + kTileM - 1) / kTileM;
   const int64_t col_tiles = (N + kTileN - 1) / kTileN;
-  T* Ahl = static_cast<T*>(workspace);
-  T* Bhl = Ahl + (size_t)row_blocks * 2 * kTileM * Kp;
+  constexpr int NT = F32 ? 3 : 2;
+  __nv_bfloat16* Ahl = static_cast<__nv_bfloat16*>(workspace);
+  __nv_bfloat16* Bhl = Ahl + (size_t)row_blocks * NT * kTileM * Kp;
   const int sms = sm_count_tc();
-  prep_b_kernel<T><<<sms * 4, 256, 0, s>>>(B, M, ld, K, Kp, row_blocks, Ahl);
-  prep_c_kernel<T><<<sms * 8, 256, 0, s>>>(C, N, K, Kp, col_tiles, Bhl);
+  prep_b_kernel<NT><<<sms * 4, 256, 0, s>>>(B, M, ld, K, Kp, row_blocks, Ahl);
+  prep_c_kernel<NT><<<sms * 8, 256, 0, s>>>(C, N, K, Kp, col_tiles, Bhl);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   TcArgs a{};
@@ -490,7 +506,14 @@ static cudaError_t launch_tc(const float* X, void* R, const float* B, const floa
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return cudaErrorInvalidValue;
   }
-  const size_t smem = tc_smem(Kp, (int)sizeof(T)).total;
+  // as many X buffers as shared memory holds beside the operand tiles
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  int xb = kMaxXBuf;
+  while (xb > 2 && tc_smem(Kp, NT, xb).total > (size_t)optin) --xb;
+  a.xbufs = xb;
+  const size_t smem = tc_smem(Kp, NT, xb).total;
   e = cudaFuncSetAttribute(refresh_tc_kernel<F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   refresh_tc_kernel<F32><<<sms, kTcThreads, smem, s>>>(a, tmX, tmR);
@@ -501,8 +524,8 @@ cudaError_t launch_refresh_tc(const float* X, void* R, const float* B, const flo
                               void* workspace, double* part, float* P1, double* CC1, int* err, uint64_t timeout_ns,
                               cudaStream_t s, bool f32) {
   if (!refresh_tc_supported(K, f32)) return cudaErrorInvalidValue;
-  return f32 ? launch_tc<float, true>(X, R, B, C, M, ld, N, K, workspace, part, P1, CC1, err, timeout_ns, s)
-             : launch_tc<__nv_bfloat16, false>(X, R, B, C, M, ld, N, K, workspace, part, P1, CC1, err, timeout_ns,
+  return f32 ? launch_tc<true>(X, R, B, C, M, ld, N, K, workspace, part, P1, CC1, err, timeout_ns, s)
+             : launch_tc<false>(X, R, B, C, M, ld, N, K, workspace, part, P1, CC1, err, timeout_ns,
                                                s);
 }
 

@@ -1,4 +1,4 @@
-"""Tensor-core refresh (tcgen05): BF16x3 for a bfloat16 residual, TF32x3 for a float32 one.
+"""Tensor-core refresh (tcgen05): BF16x3 for a bfloat16 residual, BF16x6 for a float32 one.
 
 R = X - B C from three bfloat16 products with float32 accumulation must equal
 the exact X - B C up to (a) the dropped Bl Cl term and the float32
@@ -72,13 +72,15 @@ def test_tensor_core_refresh_in_a_bf16_run(did):
     assert abs(f_tc - f_simt) <= 1e-3 * f_simt
 
 
-# ------------------------------------------------- TF32x3 (float32 residual)
+# ------------------------------------------------- BF16x6 (float32 residual)
 @pytest.mark.parametrize("M,N,K", [(200, 1000, 10), (517, 777, 64), (128, 64, 16), (5000, 2100, 50), (129, 130, 64),
                                    (300, 500, 3)])
 def test_tensor_core_refresh_fp32_matches_product(did, M, N, K):
-    """TF32x3: Bh Ch + Bh Cl + Bl Ch with Bh the operand rounded to 11
-    significand bits; the remainders are read as TF32 (11 bits), so a product
-    is off by about 2^-21 relative, plus float32 accumulation over Kp terms."""
+    """BF16x6: each float32 operand as three bfloat16 terms and the six
+    products whose terms reach 2^-18 of the leading one, accumulated in
+    float32: a product is off by about 2^-26 relative, and the float32
+    accumulation of the 6 Kp / 16 MMAs adds at most about 2^-18 of sum |B||C|;
+    the bound below allows 2^-17 of it."""
     X, _, _ = W.planted(M, N, K, seed=2 * M + N, sigma=0.01)
     B0, C0 = W.init_factors(M, N, K, 9)
     Xc = np.ascontiguousarray(X.T)
@@ -94,7 +96,7 @@ def test_tensor_core_refresh_fp32_matches_product(did, M, N, K):
     R_exact = X.astype(np.float64) - B0.astype(np.float64) @ C0.astype(np.float64)
     bound = 2.0 ** -17 * absP + 2.0 ** -22 * np.abs(R_exact)
     err = np.abs(R_tc - R_exact)
-    print("TF32x3 M=%d N=%d K=%d: max err/|BC| %.3g, max err/bound %.3g, SIMT max err/|BC| %.3g, f rel %.3g"
+    print("BF16x6 M=%d N=%d K=%d: max err/|BC| %.3g, max err/bound %.3g, SIMT max err/|BC| %.3g, f rel %.3g"
           % (M, N, K, (err / absP).max(), (err / bound).max(), (np.abs(R_simt - R_exact) / absP).max(),
              abs(f_tc - f_simt) / f_simt))
     assert np.all(err <= bound)
@@ -128,7 +130,7 @@ def test_tensor_core_refresh_in_an_fp32_run(did):
         n_tc = ctx.info()["tc_refreshes"]
     eB = np.linalg.norm(B - ref["B"]) / np.linalg.norm(ref["B"])
     eF = float(np.max(np.abs(t - ref["trace"]) / ref["trace"]))
-    print("FP32 20 sweeps, TF32x3 refresh every 2: tc refreshes %d, relB %.3g, max relf %.3g" % (n_tc, eB, eF))
+    print("FP32 20 sweeps, BF16x6 refresh every 2: tc refreshes %d, relB %.3g, max relf %.3g" % (n_tc, eB, eF))
     assert n_tc == 10
     assert eB <= 1e-4 and eF <= 1e-5
 
