@@ -30,9 +30,14 @@
 // split into three bfloat16 terms (tc::split_bf16x3) and the six partial
 // products whose terms reach 2^-18 of the leading one are accumulated in
 // float32, which matches float32 arithmetic (the residual is updated in
-// place for many sweeps, so its products need float32 accuracy; a TF32x3
-// split, about 2^-20 per product, let the residual drift by 4.5e-5 of the
-// objective in 20 sweeps on a near-exact fit).
+// place for many sweeps, so its products need float32 accuracy).
+//
+// The float32 accumulator of tcgen05 does not round to nearest, so a long
+// chain of MMA additions drifts: g summed over 5000 rows in one accumulator
+// moved B and C by 4.9e-5 of the float64 result in 20 sweeps.  The g pass
+// therefore drains its accumulator into float32 sums on the CUDA cores every
+// four 32-row chunks, and the update pass its W accumulator every eight
+// tiles, each into a second accumulator set so the MMAs do not wait.
 //
 // Kernels of one sweep (K <= 64):
 //   prep_gb     B -> bfloat16 x3 tiles of 32 rows for the g pass (1 MB at K = 50)
