@@ -179,8 +179,9 @@ bool make_plan(int ld, int64_t N, int K, BPlan* p) {
     P.gsmem = std::max(kMinSmem, P.grs * P.grstage + P.gbs * P.gbstage + fixed);
   }
   // update pass: 64-column tiles where tensor memory holds them, else 32
-  // (columns: two accumulators, two E' buffers of three terms, two W sets, three Y terms)
-  auto tmem_cols = [&](int nu) { return 2 * nu + 3 * nu + 2 * P.KN + 3 * P.Z16 / 2; };
+  // (columns: the accumulator of three ranges, two E' buffers of three terms,
+  // two W sets, three Y terms)
+  auto tmem_cols = [&](int nu) { return 3 * nu + 3 * nu + 2 * P.KN + 3 * P.Z16 / 2; };
   P.nu = tmem_cols(64) <= (int)kTmemCols ? 64 : 32;
   if (tmem_cols(P.nu) > (int)kTmemCols) return false;
   P.utiles = (N + P.nu - 1) / P.nu;
@@ -644,7 +645,7 @@ struct UArgs {
 //   RFULL[r] (1, tx), REMPTY[r] (1)   R ring (the store warp releases)
 //   EPIDONE[r] (8)                    the tile of E' in R buffer r is complete
 //   ZFULL[z] (1, tx), ZEMPTY[z] (1)   operand ring (W commit releases)
-//   ACCFULL[x] (1), ACCEMPTY[x] (8)   accumulators of Y Z
+//   ACCFULL (1), ACCEMPTY (8)         the accumulator of Y Z (one, three ranges)
 //   EREADY[x] (8), EFREE[x] (1)       E' buffers (three terms each) in TMEM
 //   YREADY (8)                        the Y row block of the next unit is in TMEM
 //   WFULL[w] (1), WEMPTY[w] (8)       W sets of alternate groups of tiles
@@ -687,11 +688,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) update_kernel(UArgs a, const __
   const size_t zpart = (size_t)nu * Z16 * 2;      // bytes of one term of the Z tile
   const size_t cpart = (size_t)KN * nu * 2;       // bytes of one term of the C'^T tile
   const size_t zbytes = 3 * zpart, cbytes = 3 * cpart;
-  // TMEM columns: two accumulators, two E' buffers (three terms of nu/2
-  // columns each), two W sets, and the three terms of the Y row block.
-  const uint32_t W0 = 5 * nu, Y0 = 5 * nu + 2 * KN;
-  auto ACC = [&](int x) { return (uint32_t)(x * nu); };
-  auto EP = [&](int x, int p) { return (uint32_t)(2 * nu + x * (3 * nu / 2) + p * (nu / 2)); };
+  // TMEM columns: the accumulator of Y Z in three ranges of nu columns,
+  // two E' buffers (three terms of nu/2 columns each), two W sets, and the
+  // three terms of the Y row block.  With the terms of the Z tile stacked
+  // along N (they lie one after another in the tile), one MMA per term of Y
+  // forms several products:
+  //   Y0 [Z0 Z1 Z2] -> ranges 0, 1, 2;  Y1 [Z0 Z1] -> ranges 1, 2;  Y2 Z0 -> range 2,
+  // so range 0 holds Y0 Z0, range 1 Y0 Z1 + Y1 Z0, range 2 the 2^-16 terms
+  // Y0 Z2 + Y1 Z1 + Y2 Z0, and Y Z = range 0 + (range 1 + range 2).  A
+  // tcgen05.mma of M = 128 costs about the same for every N up to 128, so
+  // three MMAs of N = 3nu, 2nu, nu per K step do the work of six of N = nu.
+  const uint32_t W0 = 6 * nu, Y0 = 6 * nu + 2 * KN;
+  auto ACC = [&](int r) { return (uint32_t)(r * nu); };
+  auto EP = [&](int x, int p) { return (uint32_t)(3 * nu + x * (3 * nu / 2) + p * (nu / 2)); };
   auto WS = [&](int w) { return W0 + (uint32_t)(w * KN); };
   auto YP = [&](int p) { return Y0 + (uint32_t)(p * (Z16 / 2)); };
 
@@ -753,7 +762,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) update_kernel(UArgs a, const __
   } else if (warp == 1) {
     // ------------------------------------------------------------- MMA issue
     if (lane == 0) {
-      const uint32_t iU = tc::instr_desc_bf16(128, nu), iW = tc::instr_desc_bf16(128, KN);
+      const uint32_t iU3 = tc::instr_desc_bf16(128, 3 * nu), iU2 = tc::instr_desc_bf16(128, 2 * nu);
+      const uint32_t iU1 = tc::instr_desc_bf16(128, nu), iW = tc::instr_desc_bf16(128, KN);
       const uint64_t zdesc_ring = tc::smem_desc(smem_u32(zring), 128u, (uint32_t)Z16 * 16u);
       const uint64_t cdesc_ring = tc::smem_desc(smem_u32(zring), 128u, (uint32_t)nu * 16u);
       int64_t i = 0;
@@ -794,9 +804,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) update_kernel(UArgs a, const __
         if (!tc::wait(bars + U_YREADY, (uint32_t)(ui & 1), err, tmo)) break;
         const int64_t ifirst = i, n = t1 - t0;
         for (int64_t t = t0; t < t1; ++t, ++i) {
-          const int s = (int)(i % ZS), x = (int)(i & 1);
+          const int s = (int)(i % ZS);
           if (!tc::wait(bars + U_ZFULL + s, (uint32_t)((i / ZS) & 1), err, tmo)) { ok = false; break; }
-          if (i >= 2 && !tc::wait(bars + U_ACCEMPTY + x, (uint32_t)(((i >> 1) - 1) & 1), err, tmo)) {
+          if (i >= 1 && !tc::wait(bars + U_ACCEMPTY, (uint32_t)((i - 1) & 1), err, tmo)) {
             ok = false;
             break;
           }
@@ -804,16 +814,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) update_kernel(UArgs a, const __
           const uint64_t zd0 = desc_add(zdesc_ring, (uint32_t)((size_t)s * a.zstage));
           const int ksteps = Z16 / 16;
 #pragma unroll
-          for (int pr = 0; pr < kProds; ++pr) {
-            const uint32_t a0 = tmem + YP(prod_a(pr));
-            const uint64_t b0 = desc_add(zd0, (uint32_t)(prod_b(pr) * zpart));
-#pragma unroll
-            for (int kk = 0; kk < kMaxK * 2 / 16; ++kk)
-              if (kk < ksteps)
-                tc::mma_bf16_tmem_a(tmem + ACC(x), a0 + (uint32_t)kk * 8u, desc_add(b0, (uint32_t)kk * 256u), iU,
-                                    (pr > 0 || kk > 0) ? 1u : 0u);
+          for (int kk = 0; kk < kMaxK * 2 / 16; ++kk) {
+            if (kk < ksteps) {
+              const uint64_t bk = desc_add(zd0, (uint32_t)kk * 256u);
+              const uint32_t ak = (uint32_t)kk * 8u;
+              tc::mma_bf16_tmem_a(tmem + ACC(0), tmem + YP(0) + ak, bk, iU3, kk > 0 ? 1u : 0u);
+              tc::mma_bf16_tmem_a(tmem + ACC(1), tmem + YP(1) + ak, bk, iU2, 1u);
+              tc::mma_bf16_tmem_a(tmem + ACC(2), tmem + YP(2) + ak, bk, iU1, 1u);
+            }
           }
-          tc::mma_commit(bars + U_ACCFULL + x);
+          tc::mma_commit(bars + U_ACCFULL);
           shared_flags[0] = 1;
           if (i > ifirst && !issue_w(i - 1, i - 1 - ifirst, n)) { ok = false; break; }
         }
@@ -925,18 +935,25 @@ __global__ void __launch_bounds__(kTcThreads, 1) update_kernel(UArgs a, const __
       const int64_t n = t1 - t0, wg_first = wgE;
       for (int64_t t = t0; t < t1 && ok; ++t, ++i) {
         const int s = (int)(i % RS), x = (int)(i & 1);
-        ok = tc::wait(bars + U_ACCFULL + x, (uint32_t)((i >> 1) & 1), err, tmo) &&
+        ok = tc::wait(bars + U_ACCFULL, (uint32_t)(i & 1), err, tmo) &&
              tc::wait(bars + U_RFULL + s, (uint32_t)((i / RS) & 1), err, tmo);
         ok = __all_sync(0xffffffffu, ok);
         if (!ok) break;
         tc::fence_after();
         float d[hc];
 #pragma unroll
-        for (int c = 0; c < hc; c += 16)
-          tc::tmem_ld<16>(tmem + lane_base + ACC(x) + (uint32_t)(h * hc + c), d + c);
+        for (int c = 0; c < hc; c += 16) {
+          float r1[16], r2[16];
+          const uint32_t col = (uint32_t)(h * hc + c);
+          tc::tmem_ld<16>(tmem + lane_base + ACC(0) + col, d + c);
+          tc::tmem_ld<16>(tmem + lane_base + ACC(1) + col, r1);
+          tc::tmem_ld<16>(tmem + lane_base + ACC(2) + col, r2);
+#pragma unroll
+          for (int u = 0; u < 16; ++u) d[c + u] += r1[u] + r2[u];
+        }
         tc::fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(bars + U_ACCEMPTY + x);
+        if (lane == 0) mbar_arrive(bars + U_ACCEMPTY);
         // E' = R_s - Y Z on this thread's row and half of the tile; written
         // back in place for the store, squared into the norm.
         float* rt = reinterpret_cast<float*>(rring + (size_t)s * a.rstage) + (size_t)(h * hc) * 128 + row;
