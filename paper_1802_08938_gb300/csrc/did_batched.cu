@@ -85,7 +85,7 @@ constexpr uint32_t kTmemCols = 512;
 // must never share an SM: every launch asks for more than half of an SM's
 // shared memory.
 constexpr size_t kMinSmem = 120 * 1024;
-constexpr int kSolveThreads = 128;
+constexpr int kSolveThreads = 256;      // eight warps, one column at a time each
 constexpr int kBThreads = 128;
 constexpr int kNormPartMax = 1024;
 
@@ -151,6 +151,8 @@ int sm_count() {
 }
 
 size_t al1024(size_t x) { return (x + 1023) & ~(size_t)1023; }
+
+size_t solve_smem(int K, int nu);
 
 bool make_plan(int ld, int64_t N, int K, BPlan* p) {
   if (K < 1 || K > kMaxK) return false;
@@ -219,7 +221,13 @@ bool make_plan(int ld, int64_t N, int K, BPlan* p) {
     if (P.urs < 3) return false;
     P.usmem = std::max(kMinSmem, P.urs * P.urstage + P.uzs * P.uzstage + fixed);
   }
-  P.sgrid = 2 * sms;
+  {
+    // column solve: as many blocks as stay resident (two per SM by its
+    // launch bounds, fewer if shared memory says so), at most one per tile
+    const size_t ss = solve_smem(K, P.nu);
+    const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(2, (size_t)(227 * 1024) / ss));
+    P.sgrid = (int)std::min<int64_t>(P.utiles, (int64_t)per_sm * sms);
+  }
   P.npairs = K * (K + 1) / 2;
   *p = P;
   return true;
@@ -501,18 +509,34 @@ struct SArgs {
 // G = B^T B.  With dl the change of the column so far (all repeats),
 //   t_i = g_ij - sum_l G_il dl_l ;  c_ij := [c_ij + t_i / G_ii]_+
 // (in the first pass dl_l = 0 for l >= i, so the sum runs over l < i).
-__global__ void __launch_bounds__(kSolveThreads) solve_c_kernel(SArgs a) {
+// Eight lanes per column, four columns per warp: lane q of a column's group
+// holds rows m = q + 8 s (s < NS, NS = ceil(K / 8)) of the column's gradient
+// r = g - (B^T D) c_old - G dl.  Step i broadcasts row i's values from its
+// lane; the group forms the update and subtracts G_mi (change of dl_i) from
+// its rows, so r_i is always the current t_i.  G and B^T D are held padded
+// to KP = 8 NS rows with zeros, so rows past K stay inert.
+// A block takes whole operand tiles of nu columns: C and g of the tile are
+// staged in shared memory by coalesced loads, the updated columns go back
+// the same way, and the tiles [C_old; dl] and C'^T (three bfloat16 terms)
+// are written as whole 16-byte rows of their core matrices.  The block also
+// sums V = C' C'^T over its tiles (float32 within a tile, float64 across).
+template <int NS>
+__global__ void __launch_bounds__(kSolveThreads, 2) solve_c_kernel(SArgs a) {
   extern __shared__ float shs[];
-  const int K = a.K;
-  float* Gs = shs;                       // K x K, G_il at Gs[i*K + l]
-  float* Hs = Gs + K * K;                // K x K, (B^T D)_il at Hs[i*K + l]
-  float* Cs = Hs + K * K;                // [128][K + 1] updated columns of the chunk
-  unsigned short* pairs = reinterpret_cast<unsigned short*>(Cs + kSolveThreads * (K + 1));
-  const int K2 = 2 * K;
-  for (int idx = threadIdx.x; idx < K * K; idx += blockDim.x) {
-    const int i = idx / K, l = idx % K;
-    Gs[idx] = a.YY[(size_t)(K + i) + (size_t)(K + l) * K2];
-    Hs[idx] = a.YY[(size_t)(K + i) + (size_t)l * K2];
+  constexpr int KP = 8 * NS;
+  const int K = a.K, nu = a.nu, K2 = 2 * K;
+  float* Gs = shs;                        // KP x KP, G_il at Gs[i*KP + l] (symmetric)
+  float* HsT = Gs + KP * KP;              // KP x KP, (B^T D)_il at HsT[l*KP + i]
+  float* c0s = HsT + KP * KP;             // [K][nu] c_old of the tile
+  float* gs = c0s + K * nu;               // [nu][K] g of the tile
+  float* cs = gs + nu * K;                // [K][nu + 1] c'
+  float* ds = cs + K * (nu + 1);          // [K][nu + 1] dl
+  unsigned short* pairs = reinterpret_cast<unsigned short*>(ds + K * (nu + 1));
+  for (int idx = threadIdx.x; idx < KP * KP; idx += blockDim.x) {
+    const int i = idx / KP, l = idx % KP;
+    const bool in = i < K && l < K;
+    Gs[idx] = in ? a.YY[(size_t)(K + i) + (size_t)(K + l) * K2] : 0.f;
+    HsT[l * KP + i] = in ? a.YY[(size_t)(K + i) + (size_t)l * K2] : 0.f;
   }
   for (int e = threadIdx.x; e < a.npairs; e += blockDim.x) {
     int i = 0, r = e;
@@ -524,77 +548,132 @@ __global__ void __launch_bounds__(kSolveThreads) solve_c_kernel(SArgs a) {
   double vacc[kPairsPerThread];
 #pragma unroll
   for (int u = 0; u < kPairsPerThread; ++u) vacc[u] = 0.0;
+  const int lane = threadIdx.x & 31, q = lane & 7;
+  const int grp = threadIdx.x >> 3;                  // column group of the block
+  constexpr int kGroups = kSolveThreads / 8;
+  const int64_t ntiles = (a.N + nu - 1) / nu;
 
-  for (int64_t j0 = (int64_t)blockIdx.x * kSolveThreads; j0 < a.N; j0 += (int64_t)gridDim.x * kSolveThreads) {
-    const int64_t j = j0 + threadIdx.x;
-    const bool valid = j < a.N;
-    float c0[kMaxK], cur[kMaxK], dl[kMaxK], t[kMaxK];
-    if (valid) {
-      const float* gj = a.g + (size_t)j * K;
-      for (int i = 0; i < K; ++i) {
-        c0[i] = cur[i] = a.C[(size_t)i * a.N + j];
-        dl[i] = 0.f;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t j0 = tile * nu;
+    const int ncols = (int)(a.N - j0 < nu ? a.N - j0 : nu);
+    for (int e = threadIdx.x; e < K * nu; e += blockDim.x) {
+      const int k = e / nu, c = e % nu;
+      c0s[e] = c < ncols ? a.C[(size_t)k * a.N + j0 + c] : 0.f;
+    }
+    // g is [N][K]: the tile's columns are one contiguous run
+    for (int e = threadIdx.x; e < nu * K; e += blockDim.x) gs[e] = e < ncols * K ? a.g[(size_t)j0 * K + e] : 0.f;
+    __syncthreads();
+    for (int c = grp; c < nu; c += kGroups) {      // uniform across a warp (nu is a multiple of 32)
+      float c0[NS], r[NS], cur[NS], d[NS];
+#pragma unroll
+      for (int t = 0; t < NS; ++t) {
+        const int m = q + 8 * t;
+        c0[t] = m < K ? c0s[m * nu + c] : 0.f;
+        r[t] = m < K ? gs[c * K + m] : 0.f;
+        cur[t] = c0[t];
+        d[t] = 0.f;
       }
       // g_j - (B^T D) c_j: the pending correction of the stored residual
-      for (int i = 0; i < K; ++i) {
-        float s = gj[i];
-        for (int l = 0; l < K; ++l) s = fmaf(-Hs[i * K + l], c0[l], s);
-        t[i] = s;
+      for (int l = 0; l < K; ++l) {
+        const float cl = c0s[l * nu + c];
+#pragma unroll
+        for (int t = 0; t < NS; ++t) r[t] = fmaf(-HsT[l * KP + q + 8 * t], cl, r[t]);
       }
-      for (int r = 0; r < a.reps; ++r) {
-        for (int i = 0; i < K; ++i) {
-          const int lend = r == 0 ? i : K;
-          float sl = 0.f;
-          for (int l = 0; l < lend; ++l) sl = fmaf(Gs[i * K + l], dl[l], sl);
-          const float gii = Gs[i * K + i];
-          if (gii > 0.f) {
-            const float v = cur[i] + (t[i] - sl) / gii;
-            cur[i] = v > 0.f ? v : 0.f;
-            dl[i] = cur[i] - c0[i];
-          } else if (j == 0) {
-            atomicAdd(a.degen, 1ull);
+      for (int rr = 0; rr < a.reps; ++rr) {
+#pragma unroll
+        for (int t = 0; t < NS; ++t) {
+          for (int o = 0; o < 8; ++o) {
+            const int i = 8 * t + o;
+            if (i >= K) break;
+            const float ri = __shfl_sync(0xffffffffu, r[t], o, 8);
+            const float ci = __shfl_sync(0xffffffffu, cur[t], o, 8);
+            const float c0i = __shfl_sync(0xffffffffu, c0[t], o, 8);
+            const float di = __shfl_sync(0xffffffffu, d[t], o, 8);
+            const float gii = Gs[i * KP + i];
+            float delta = 0.f;
+            if (gii > 0.f) {
+              const float v = ci + ri / gii;
+              const float nc = v > 0.f ? v : 0.f;
+              const float nd = nc - c0i;
+              delta = nd - di;
+              if (q == o) {
+                cur[t] = nc;
+                d[t] = nd;
+              }
+            } else if (j0 + c == 0 && q == 0) {
+              atomicAdd(a.degen, 1ull);
+            }
+#pragma unroll
+            for (int u = 0; u < NS; ++u) r[u] = fmaf(-Gs[i * KP + q + 8 * u], delta, r[u]);
           }
         }
       }
-      for (int i = 0; i < K; ++i) a.C[(size_t)i * a.N + j] = cur[i];
-      // operand tiles of the update pass (three bfloat16 terms each)
-      const int64_t tile = j / a.nu;
-      const int cl = (int)(j % a.nu);
-      __nv_bfloat16* zb = a.Zt + (size_t)tile * 3 * a.nu * a.Z16;
-      const size_t zpart = (size_t)a.nu * a.Z16;
-      for (int kk = 0; kk < a.Z16; ++kk) {
-        const float v = kk < K ? c0[kk] : (kk < K2 ? dl[kk - K] : 0.f);
-        __nv_bfloat16 p0, p1, p2;
-        tc::split_bf16x3(v, p0, p1, p2);
-        const size_t o = tiled2(cl, kk, a.Z16);
-        zb[o] = p0;
-        zb[zpart + o] = p1;
-        zb[2 * zpart + o] = p2;
-      }
-      __nv_bfloat16* cb = a.Ct + (size_t)tile * 3 * a.KN * a.nu;
-      const size_t cpart = (size_t)a.KN * a.nu;
-      for (int k = 0; k < a.KN; ++k) {
-        const float v = k < K ? cur[k] : 0.f;
-        __nv_bfloat16 p0, p1, p2;
-        tc::split_bf16x3(v, p0, p1, p2);
-        const size_t o = tiled2(k, cl, a.nu);
-        cb[o] = p0;
-        cb[cpart + o] = p1;
-        cb[2 * cpart + o] = p2;
+#pragma unroll
+      for (int t = 0; t < NS; ++t) {
+        const int m = q + 8 * t;
+        if (m < K) {
+          const bool in = c < ncols;
+          cs[m * (nu + 1) + c] = in ? cur[t] : 0.f;
+          ds[m * (nu + 1) + c] = in ? d[t] : 0.f;
+        }
       }
     }
-    for (int i = 0; i < K; ++i) Cs[threadIdx.x * (K + 1) + i] = valid ? cur[i] : 0.f;
     __syncthreads();
-    // V partials: this thread's pairs over the chunk's 128 columns (float32
-    // within the chunk, float64 across chunks)
+    for (int e = threadIdx.x; e < K * nu; e += blockDim.x) {
+      const int k = e / nu, c = e % nu;
+      if (c < ncols) a.C[(size_t)k * a.N + j0 + c] = cs[k * (nu + 1) + c];
+    }
+    // operand tiles of the update pass: row w of 8 elements (16 bytes) of a
+    // core matrix at element 8 w
+    {
+      __nv_bfloat16* zb = a.Zt + (size_t)tile * 3 * nu * a.Z16;
+      const size_t zpart = (size_t)nu * a.Z16;
+      const int zk8 = a.Z16 / 8;
+      for (int w = threadIdx.x; w < nu * zk8; w += blockDim.x) {
+        const int cl = (w / 8 / zk8) * 8 + (w & 7);
+        const int kk0 = ((w / 8) % zk8) * 8;
+        uint32_t w0[4], w1[4], w2[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          float v[2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int kk = kk0 + 2 * u + h;
+            v[h] = kk < K ? c0s[kk * nu + cl] : (kk < K2 ? ds[(kk - K) * (nu + 1) + cl] : 0.f);
+          }
+          split_pair(v[0], v[1], w0[u], w1[u], w2[u]);
+        }
+        *reinterpret_cast<uint4*>(zb + (size_t)w * 8) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+        *reinterpret_cast<uint4*>(zb + zpart + (size_t)w * 8) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+        *reinterpret_cast<uint4*>(zb + 2 * zpart + (size_t)w * 8) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+      }
+      __nv_bfloat16* cb = a.Ct + (size_t)tile * 3 * a.KN * nu;
+      const size_t cpart = (size_t)a.KN * nu;
+      const int n8 = nu / 8;
+      for (int w = threadIdx.x; w < a.KN * n8; w += blockDim.x) {
+        const int k = (w / 8 / n8) * 8 + (w & 7);
+        const int cl0 = ((w / 8) % n8) * 8;
+        uint32_t w0[4], w1[4], w2[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float va = k < K ? cs[k * (nu + 1) + cl0 + 2 * u] : 0.f;
+          const float vb = k < K ? cs[k * (nu + 1) + cl0 + 2 * u + 1] : 0.f;
+          split_pair(va, vb, w0[u], w1[u], w2[u]);
+        }
+        *reinterpret_cast<uint4*>(cb + (size_t)w * 8) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+        *reinterpret_cast<uint4*>(cb + cpart + (size_t)w * 8) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+        *reinterpret_cast<uint4*>(cb + 2 * cpart + (size_t)w * 8) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+      }
+    }
+    // V partials: this thread's pairs over the tile's columns
 #pragma unroll
     for (int u = 0; u < kPairsPerThread; ++u) {
       const int e = threadIdx.x + u * kSolveThreads;
       if (e < a.npairs) {
         const int i = pairs[e] >> 8, l = pairs[e] & 255;
-        float s = 0.f;
-        for (int col = 0; col < kSolveThreads; ++col) s = fmaf(Cs[col * (K + 1) + i], Cs[col * (K + 1) + l], s);
-        vacc[u] += (double)s;
+        float sv = 0.f;
+        for (int col = 0; col < ncols; ++col) sv = fmaf(cs[i * (nu + 1) + col], cs[l * (nu + 1) + col], sv);
+        vacc[u] += (double)sv;
       }
     }
     __syncthreads();
@@ -606,8 +685,46 @@ __global__ void __launch_bounds__(kSolveThreads) solve_c_kernel(SArgs a) {
   }
 }
 
-size_t solve_smem(int K) {
-  return (size_t)2 * K * K * 4 + (size_t)kSolveThreads * (K + 1) * 4 + (size_t)(K * (K + 1) / 2) * 2 + 16;
+size_t solve_smem(int K, int nu) {
+  const size_t kp = (size_t)(K + 7) / 8 * 8;
+  return ((size_t)2 * kp * kp + (size_t)2 * K * nu + (size_t)2 * K * (nu + 1)) * 4 + (size_t)(K * (K + 1) / 2) * 2 + 16;
+}
+
+// The solve instantiated for ceil(K / 8) slots of rows per lane.
+template <int NS>
+cudaError_t launch_solve_ns(const SArgs& sa, int grid, size_t smem, cudaStream_t s) {
+  solve_c_kernel<NS><<<grid, kSolveThreads, smem, s>>>(sa);
+  return cudaGetLastError();
+}
+cudaError_t launch_solve(const SArgs& sa, int grid, cudaStream_t s) {
+  const size_t smem = solve_smem(sa.K, sa.nu);
+  switch ((sa.K + 7) / 8) {
+    case 1: return launch_solve_ns<1>(sa, grid, smem, s);
+    case 2: return launch_solve_ns<2>(sa, grid, smem, s);
+    case 3: return launch_solve_ns<3>(sa, grid, smem, s);
+    case 4: return launch_solve_ns<4>(sa, grid, smem, s);
+    case 5: return launch_solve_ns<5>(sa, grid, smem, s);
+    case 6: return launch_solve_ns<6>(sa, grid, smem, s);
+    case 7: return launch_solve_ns<7>(sa, grid, smem, s);
+    case 8: return launch_solve_ns<8>(sa, grid, smem, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+cudaError_t set_solve_smem(int K, int nu) {
+  const int smem = (int)solve_smem(K, nu);
+  cudaError_t e = cudaSuccess;
+  switch ((K + 7) / 8) {
+    case 1: e = cudaFuncSetAttribute(solve_c_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); break;
+    case 2: e = cudaFuncSetAttribute(solve_c_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); break;
+    case 3: e = cudaFuncSetAttribute(solve_c_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); break;
+    case 4: e = cudaFuncSetAttribute(solve_c_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); break;
+    case 5: e = cudaFuncSetAttribute(solve_c_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); break;
+    case 6: e = cudaFuncSetAttribute(solve_c_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); break;
+    case 7: e = cudaFuncSetAttribute(solve_c_kernel<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); break;
+    case 8: e = cudaFuncSetAttribute(solve_c_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); break;
+    default: e = cudaErrorInvalidValue;
+  }
+  return e;
 }
 
 // V (K x K, symmetric, float32) from the solve blocks' partials, added in block order.
@@ -945,9 +1062,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) update_kernel(UArgs a, const __
         for (int c = 0; c < hc; c += 16) {
           float r1[16], r2[16];
           const uint32_t col = (uint32_t)(h * hc + c);
-          tc::tmem_ld<16>(tmem + lane_base + ACC(0) + col, d + c);
-          tc::tmem_ld<16>(tmem + lane_base + ACC(1) + col, r1);
-          tc::tmem_ld<16>(tmem + lane_base + ACC(2) + col, r2);
+          tc::tmem_ld3x16(tmem + lane_base + ACC(0) + col, tmem + lane_base + ACC(1) + col,
+                          tmem + lane_base + ACC(2) + col, d + c, r1, r2);
 #pragma unroll
           for (int u = 0; u < 16; ++u) d[c + u] += r1[u] + r2[u];
         }
@@ -1248,8 +1364,7 @@ BatchedState* batched_create(void* ws, int ld, int64_t N, int K, cudaStream_t s)
       cudaFuncSetAttribute(g_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess ||
       cudaFuncSetAttribute(update_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess ||
       cudaFuncSetAttribute(update_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess ||
-      cudaFuncSetAttribute(solve_c_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)solve_smem(K)) !=
-          cudaSuccess ||
+      set_solve_smem(K, b->P.nu) != cudaSuccess ||
       cudaFuncSetAttribute(update_b_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, K * K * 4) != cudaSuccess) {
     cudaGetLastError();
     delete b;
@@ -1338,8 +1453,7 @@ cudaError_t batched_sweep(BatchedState* b, float* R, float* Y, float* C, int ld,
   sa.reps = reps_c;
   sa.npairs = P.npairs;
   sa.N = N;
-  solve_c_kernel<<<P.sgrid, kSolveThreads, solve_smem(K), s>>>(sa);
-  e = cudaGetLastError();
+  e = launch_solve(sa, P.sgrid, s);
   if (e != cudaSuccess) return e;
   vreduce_kernel<<<(P.npairs + 127) / 128, 128, 0, s>>>(b->Vp, P.sgrid, P.npairs, K, b->V);
   e = cudaGetLastError();

@@ -122,6 +122,41 @@ __device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Three loads of 16 columns in flight at once, one wait: the registers are
+// tied to the wait through empty asm statements, so no use of them can be
+// scheduled before it.
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void regs_after_wait16(uint32_t* r) {
+  asm volatile(""
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                 "+r"(r[15])
+               :
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld3x16(uint32_t t0, uint32_t t1, uint32_t t2, float* v0, float* v1, float* v2) {
+  uint32_t a[16], b[16], c[16];
+  tmem_ld16_nowait(t0, a);
+  tmem_ld16_nowait(t1, b);
+  tmem_ld16_nowait(t2, c);
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  regs_after_wait16(a);
+  regs_after_wait16(b);
+  regs_after_wait16(c);
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    v0[i] = __uint_as_float(a[i]);
+    v1[i] = __uint_as_float(b[i]);
+    v2[i] = __uint_as_float(c[i]);
+  }
+}
+
 // N consecutive float32 columns into this thread's TMEM lane (warp-collective).
 // The stores are asynchronous: tmem_st_wait() completes them, and a following
 // fence_before + mbarrier arrive publishes the values to the MMA thread.
