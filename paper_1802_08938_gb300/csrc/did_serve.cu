@@ -34,6 +34,9 @@ constexpr uint64_t kServeTimeoutNs = 4000000000ull;
 constexpr double kPassFixedS = 12e-6;
 constexpr double kCtaBytesPerS = 40e9;
 constexpr double kRoundMinS = 5e-3;      // a round lasts at least this long
+// Phase stamps kept per instance (4 per k of its first sweep in a round):
+// the measured time of that sweep drives the next round's CTA shares.
+constexpr int kStampK = 64;
 
 double now_s(const std::chrono::steady_clock::time_point& t0) {
   return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -56,6 +59,8 @@ struct Req {
   void* R = nullptr;
   double *CCp = nullptr, *Sp = nullptr, *OBJp = nullptr;
   int sweeps = 0;
+  double cta_s = -1.0;     // measured CTA-seconds per sweep (smoothed); < 0: not measured yet
+  int sh_last = 0;         // CTAs of its last round (0: none yet)
   std::vector<double> trace;
   std::vector<float> Bh, Ch;   // results on the host after completion
   double t_submit = 0, t_start = 0, t_done = 0;
@@ -91,6 +96,8 @@ struct did_server {
   Ctrl* h_ctrl = nullptr;
   double* d_trace = nullptr;
   double* h_trace = nullptr;
+  uint64_t* d_stamp = nullptr;       // [slot][4 kStampK] phase stamps of an instance's first sweep
+  uint64_t* h_stamp = nullptr;
   unsigned long long* d_degen = nullptr;
   unsigned long long* d_bad = nullptr;   // negative or non-finite entries of a request's X
   unsigned long long* h_bad = nullptr;
@@ -210,14 +217,24 @@ void release(did_server* s, Req* r) {
   }
 }
 
-// Split the launch's CTAs among the active requests by per-sweep work.
+// CTA-seconds one sweep of a request takes: measured in earlier rounds, else
+// from the cost model at one CTA (its column passes' bytes at one CTA's share
+// of the bandwidth, plus the fixed part of each pass).
+double sweep_cta_s(const did_server* s, const Req* r) {
+  if (r->cta_s > 0.0) return r->cta_s;
+  const double pass_bytes = 2.0 * (double)r->ld * (double)r->rq.N * (s->bf16 ? 2.0 : 4.0);
+  return (double)r->rq.K * (kPassFixedS + pass_bytes / kCtaBytesPerS);
+}
+
+// Split the launch's CTAs among the active requests in proportion to the
+// CTA-seconds their sweeps take, so that their sweeps take about equally long.
 std::vector<int> shares(const did_server* s, const std::vector<Req*>& act) {
   const int n = (int)act.size();
   std::vector<int> sh(n, 1);
   double total = 0.0;
   std::vector<double> w(n);
   for (int i = 0; i < n; ++i) {
-    w[i] = (double)act[i]->rq.M * (double)act[i]->rq.N * (double)act[i]->rq.K;
+    w[i] = sweep_cta_s(s, act[i]);
     total += w[i];
   }
   int left = s->grid - n;
@@ -245,13 +262,12 @@ bool run_round(did_server* s, std::vector<Req*>& act) {
   const std::vector<int> sh = shares(s, act);
   // Sweeps per instance: the round lasts about as long as the slowest
   // instance's single sweep (at least kRoundMinS); faster instances run more
-  // sweeps in that time, so no CTA range idles for long.
+  // sweeps in that time, so no CTA range idles for long.  A sweep's time on
+  // sh CTAs is taken as its CTA-seconds / sh.
   std::vector<double> tsw(n);
   double T = kRoundMinS;
   for (int i = 0; i < n; ++i) {
-    const Req* r = act[i];
-    const double pass_bytes = 2.0 * (double)r->ld * (double)r->rq.N * (s->bf16 ? 2.0 : 4.0);
-    tsw[i] = (double)r->rq.K * (kPassFixedS + pass_bytes / ((double)sh[i] * kCtaBytesPerS));
+    tsw[i] = sweep_cta_s(s, act[i]) / (double)sh[i];
     T = std::max(T, tsw[i]);
   }
   std::vector<int> nsw(n);
@@ -290,7 +306,12 @@ bool run_round(did_server* s, std::vector<Req*>& act) {
     a.dynamic = 0;
     a.npart = plan.npart;
     a.n_sweeps = nsw[i];
-    a.prologue = 1;          // the CTA split may change between rounds
+    // the partials of R c_1^T left by the last sweep are valid while the
+    // instance keeps its CTA range size (same plan); else a prologue pass
+    a.prologue = sh[i] != r->sh_last ? 1 : 0;
+    r->sh_last = sh[i];
+    a.tstamp = s->d_stamp + (size_t)i * 4 * kStampK;
+    a.tstamp_cap = std::min(r->rq.K, kStampK);
     a.f_prev = r->trace.back();
     a.f0 = r->trace.front();
     a.stop_rule = r->rq.tol > 0.0 ? 1 : 0;
@@ -312,10 +333,23 @@ bool run_round(did_server* s, std::vector<Req*>& act) {
   if (e == cudaSuccess) e = cudaMemcpyAsync(s->h_ctrl, s->d_ctrl, sizeof(Ctrl) * n, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(s->h_trace, s->d_trace, sizeof(double) * n * s->round_sweeps, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s->h_stamp, s->d_stamp, sizeof(uint64_t) * n * 4 * kStampK, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return false;
+  }
+  // the first sweep's time (its first kc k-steps, scaled to K) in CTA-seconds
+  for (int i = 0; i < n; ++i) {
+    Req* r = act[i];
+    if (s->h_ctrl[i].sweeps < 1 || s->h_ctrl[i].err != 0) continue;
+    const int kc = std::min(r->rq.K, kStampK);
+    const uint64_t* st4 = s->h_stamp + (size_t)i * 4 * kStampK;
+    const uint64_t t0 = st4[0], t1 = st4[4 * (kc - 1) + 3];
+    if (t1 <= t0) continue;
+    const double cs = (double)(t1 - t0) * 1e-9 * ((double)r->rq.K / kc) * (double)sh[i];
+    r->cta_s = r->cta_s > 0.0 ? 0.5 * (r->cta_s + cs) : cs;
   }
   float ms = 0.f;
   cudaEventElapsedTime(&ms, s->ev0, s->ev1);
@@ -450,6 +484,8 @@ did_status did_server_create(size_t hbm_budget_bytes, did_precision precision, i
   ok = ok && cudaMallocHost(&s->h_ctrl, sizeof(Ctrl) * S) == cudaSuccess;
   ok = ok && cudaMalloc(&s->d_trace, sizeof(double) * S * round_sweeps) == cudaSuccess;
   ok = ok && cudaMallocHost(&s->h_trace, sizeof(double) * S * round_sweeps) == cudaSuccess;
+  ok = ok && cudaMalloc(&s->d_stamp, sizeof(uint64_t) * S * 4 * kStampK) == cudaSuccess;
+  ok = ok && cudaMallocHost(&s->h_stamp, sizeof(uint64_t) * S * 4 * kStampK) == cudaSuccess;
   ok = ok && cudaMalloc(&s->d_degen, sizeof(unsigned long long) * S) == cudaSuccess;
   ok = ok && cudaMalloc(&s->d_bad, sizeof(unsigned long long)) == cudaSuccess;
   ok = ok && cudaMallocHost(&s->h_bad, sizeof(unsigned long long)) == cudaSuccess;
@@ -589,6 +625,8 @@ void did_server_destroy(did_server* s) {
   cudaFreeHost(s->h_ctrl);
   cudaFree(s->d_trace);
   cudaFreeHost(s->h_trace);
+  cudaFree(s->d_stamp);
+  cudaFreeHost(s->h_stamp);
   cudaFree(s->d_degen);
   cudaFree(s->d_bad);
   cudaFreeHost(s->h_bad);
