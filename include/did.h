@@ -302,8 +302,13 @@ did_status did_generate_uniform(float* out_dev, int64_t n, uint64_t seed, int32_
  * budget.  Admitted requests keep X, R, B and C resident on the device.  The
  * worker runs rounds: one cooperative launch of the multi-instance sweep
  * kernel runs up to `round_sweeps` sweeps of every active request, each on
- * its own range of CTAs (sized by its work) with its own grid barriers and
- * stopping test (|f_{t-1} - f_t| / f_{t-1} < tol, or max_iter sweeps).
+ * its own range of CTAs with its own grid barriers and stopping test
+ * (|f_{t-1} - f_t| / f_{t-1} < tol, or max_iter sweeps).  A request's range
+ * is sized by the time its sweeps take: the kernel stamps the first sweep of
+ * each request in a round, and the next round gives each request CTAs in
+ * proportion to its measured CTA-seconds per sweep (a cost model of its
+ * bytes until it has run once), so the requests' sweeps take about equally
+ * long.
  * Between rounds, finished requests are retired (B, C copied to host memory
  * owned by the server, device memory freed) and waiting ones admitted, so
  * requests arriving while others run join at the next round.  The start

@@ -77,7 +77,8 @@ namespace {
 constexpr int kMaxK = 64;             // tensor-memory budget of the update pass
 constexpr int kTcThreads = 384;       // warp 0 producer, warp 1 MMA, 2-3 idle, 4-11 split / epilogue
 constexpr int kWorkWarps = 8;
-constexpr int kGChunk = 32;           // rows of R_s per g stage (128 bytes of a column)
+constexpr int kGChunk = 64;           // rows of R_s per g stage (256 bytes of a column)
+constexpr int kGBox = 32;             // rows per tensor copy (128 bytes: the 128-byte swizzle's span)
 constexpr int kGMaxRing = 8;          // most stages of a ring of the g pass
 constexpr int kURingMax = 8;          // most stages of the R ring of the update pass
 constexpr uint32_t kTmemCols = 512;
@@ -98,10 +99,6 @@ __host__ __device__ __forceinline__ size_t tiled2(int r, int c, int kp) {
   return ((size_t)(r >> 3) * (size_t)(kp >> 3) + (size_t)(c >> 3)) * 64 + (size_t)((r & 7) * 8 + (c & 7));
 }
 
-// The six products (i, j), i + j <= 2, of two three-term splits.
-constexpr int kProds = 6;
-__host__ __device__ constexpr int prod_a(int pr) { return pr == 2 || pr == 4 ? 1 : (pr == 5 ? 2 : 0); }
-__host__ __device__ constexpr int prod_b(int pr) { return pr == 1 || pr == 4 ? 1 : (pr == 3 ? 2 : 0); }
 
 // Shared-memory descriptors differ only in their start address field (bits
 // 0-13, address >> 4): a descriptor is advanced by adding the byte offset >> 4
@@ -129,7 +126,7 @@ struct BPlan {
   int M, ld, K, KN, Z16;  // KN = K rounded up to 16 (N of the g and W products); Z16 = 2K rounded up to 16
   int64_t N;
   // g pass
-  int nt;                 // columns per g tile (<= 256)
+  int nt;                 // columns per g tile (<= 128)
   int64_t gtiles;
   int mchunks;            // ceil(ld / 32)
   int ggrid, grs, gbs;
@@ -163,18 +160,19 @@ bool make_plan(int ld, int64_t N, int K, BPlan* p) {
   P.K = K;
   P.KN = (K + 15) / 16 * 16;
   P.Z16 = (2 * K + 15) / 16 * 16;
-  // g pass: tiles of nt <= 256 columns, as many as fill whole waves of the grid
-  const int64_t waves = std::max<int64_t>(1, (N + (int64_t)sms * 256 - 1) / ((int64_t)sms * 256));
+  // g pass: tiles of nt <= 128 columns (one MMA of M = 128), as many as
+  // fill whole waves of the grid
+  const int64_t waves = std::max<int64_t>(1, (N + (int64_t)sms * 128 - 1) / ((int64_t)sms * 128));
   int64_t nt = (N + waves * sms - 1) / (waves * sms);
   nt = (nt + 15) / 16 * 16;
-  P.nt = (int)std::min<int64_t>(256, std::max<int64_t>(16, nt));
+  P.nt = (int)std::min<int64_t>(128, std::max<int64_t>(16, nt));
   P.gtiles = (N + P.nt - 1) / P.nt;
   P.mchunks = (ld + kGChunk - 1) / kGChunk;
   P.ggrid = (int)std::min<int64_t>(sms, P.gtiles);
-  P.grstage = al1024((size_t)P.nt * 128);
-  P.gbstage = al1024((size_t)P.KN * 192);
+  P.grstage = al1024((size_t)P.nt * kGChunk * 4);
+  P.gbstage = al1024((size_t)P.KN * kGChunk * 2 * 3);
   {
-    const size_t fixed = (size_t)P.KN * 256 * 4 + 1024 + 1024;   // running sums, alignment, barriers
+    const size_t fixed = (size_t)P.KN * 128 * 4 + 1024 + 1024;   // running sums, alignment, barriers
     P.gbs = 3;
     P.grs = (int)std::min<size_t>(kGMaxRing, (227 * 1024 - fixed - P.gbs * P.gbstage) / P.grstage);
     if (P.grs < 2) return false;
@@ -234,9 +232,9 @@ bool make_plan(int ld, int64_t N, int K, BPlan* p) {
 }
 
 // ------------------------------------------------------------- prep_gb
-// B (ld x K column-major) -> [chunk][term][KN x 32] bfloat16 tiles for the g
+// B (ld x K column-major) -> [chunk][term][KN x 64] bfloat16 tiles for the g
 // pass: rows of the operand are k (the N of the product), the contraction is
-// the chunk's 32 rows of B.
+// the chunk's 64 rows of B.
 __global__ void prep_gb_kernel(const float* __restrict__ B, int M, int ld, int K, int KN, int mchunks,
                                __nv_bfloat16* __restrict__ out) {
   const int64_t n = (int64_t)mchunks * KN * kGChunk;
@@ -259,7 +257,7 @@ __global__ void prep_gb_kernel(const float* __restrict__ B, int M, int ld, int K
 
 // -------------------------------------------------------------- g pass
 struct GArgs {
-  const __nv_bfloat16* Bg;   // [mchunks][3][KN x 32] tiles
+  const __nv_bfloat16* Bg;   // [mchunks][3][KN x 64] tiles
   float* g;          // [N][K]: g_j contiguous
   int* err;
   int ld, K, KN, nt, mchunks;
@@ -281,26 +279,36 @@ enum { G_RFULL = 0, G_REMPTY = kGMaxRing, G_BFULL = 2 * kGMaxRing, G_BEMPTY = 3 
        G_SREADY = 4 * kGMaxRing, G_SFREE = G_SREADY + 2, G_ACCFULL = G_SFREE + 2, G_ACCEMPTY = G_ACCFULL + 2,
        G_DRAIN = G_ACCEMPTY + 2, G_NBARS };
 
-// Chunks of one accumulation group: the tensor cores sum a group's products
-// in a TMEM accumulator, and the split warps add the group totals in float32
-// (round to nearest) in shared memory.  Short accumulator chains keep the
-// tensor core's own float32 accumulation, which does not round to nearest,
-// from biasing g over M rows.
-constexpr int kGGroup = 4;
+// Chunks of one accumulation group: the tensor cores sum a group's
+// products in a TMEM accumulator, and the split warps add the group totals in
+// float32 (round to nearest) in shared memory.  Short accumulator chains keep
+// the tensor core's own float32 accumulation, which does not round to
+// nearest, from biasing g over M rows (two chunks: 128 rows, 8 K steps).
+constexpr int kGGroup = 2;
 
+// g^T = R_s^T B over tiles of nt <= 128 columns and chunks of 64 rows.  The
+// chunk's columns are the M = 128 rows of the products (TMEM lanes); the
+// split warps put its three bfloat16 terms R0, R1, R2 into TMEM as the A
+// operand.  The B chunk's terms lie one after another in shared memory, so
+// the first two stacked along N form one operand of 2KN rows:
+//   R0 [B0 B1] and R1 [B0 B1] -> ranges 0, 1;  R0 B2 and R2 B0 -> range 1,
+// range 0 holding R0 B0 + R1 B0, range 1 the other four products, and
+// g = range 0 + range 1.  Four MMAs of N = 2KN, 2KN, KN, KN per K step do
+// the work of six of N = KN (an MMA of M = 128 costs about the same for
+// every N up to 128).
 __global__ void __launch_bounds__(kTcThreads, 1) g_kernel(GArgs a, const __grid_constant__ CUtensorMap tmR) {
   extern __shared__ unsigned char sm_raw[];
   unsigned char* sm = align1024(sm_raw);
   unsigned char* rring = sm;                                                   // R chunks
   unsigned char* bring = sm + (size_t)a.rs * a.rstage;                         // B chunks
-  float* gsum = reinterpret_cast<float*>(bring + (size_t)a.bs * a.bstage);     // [KN][256] running sums
-  uint64_t* bars = reinterpret_cast<uint64_t*>(gsum + (size_t)a.KN * 256);
+  float* gsum = reinterpret_cast<float*>(bring + (size_t)a.bs * a.bstage);     // [KN][128] running sums
+  uint64_t* bars = reinterpret_cast<uint64_t*>(gsum + (size_t)a.KN * 128);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + G_NBARS);
   int* shared_flags = reinterpret_cast<int*>(tmem_slot + 4);   // [0] MMA chunks issued
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int KN = a.KN;
-  const size_t rbytes = (size_t)a.nt * 128;
+  const size_t hbytes = (size_t)a.nt * kGBox * 4;    // one tensor copy: 32 rows of the tile
   if (threadIdx.x == 0) {
     shared_flags[0] = 0;
     for (int i = 0; i < G_NBARS; ++i) {
@@ -315,11 +323,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) g_kernel(GArgs a, const __grid_
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = *tmem_slot;
-  // TMEM columns: accumulator set x (of alternate groups), half h at
-  // 2KN x + KN h; staging buffer b at 4KN + 96 b, half h at +48 h, term p at
-  // +16 p (32 bfloat16 rows in 16 columns).
-  auto accum = [&](int x, int h) { return (uint32_t)(2 * KN * x + KN * h); };
-  auto staging = [&](int b, int h) { return (uint32_t)(4 * KN + 96 * b + 48 * h); };
+  // TMEM columns: accumulator set x (of alternate groups) at 2KN x, range r
+  // at +KN r; staging buffer b at 4KN + 96 b, term p at +32 p (64 bfloat16
+  // rows in 32 columns).
+  auto accum = [&](int x, int r) { return (uint32_t)(2 * KN * x + KN * r); };
+  auto staging = [&](int b) { return (uint32_t)(4 * KN + 96 * b); };
 
   const int64_t ntile = a.gtiles > blockIdx.x ? (a.gtiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const int64_t total = ntile * a.mchunks;
@@ -328,13 +336,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) g_kernel(GArgs a, const __grid_
   const uint64_t tmo = a.timeout_ns;
 
   if (warp == 0 || warp == 3) {
-    // producers: warp 0 the R chunks (2-D TMA, 128-byte swizzle), warp 3 the
-    // B chunks (bulk copies from L2)
+    // producers: warp 0 the R chunks (two 2-D tensor copies of 32 rows each,
+    // 128-byte swizzle), warp 3 the B chunks (bulk copies from L2)
     if (lane == 0) {
       const bool rprod = warp == 0;
       const int ring = rprod ? a.rs : a.bs;
       uint64_t* full = bars + (rprod ? G_RFULL : G_BFULL);
       uint64_t* empty = bars + (rprod ? G_REMPTY : G_BEMPTY);
+      const uint32_t bbytes = (uint32_t)KN * kGChunk * 2 * 3;
       int64_t c = 0;
       for (; c < total; ++c) {
         const int64_t ti = c / a.mchunks;
@@ -343,11 +352,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) g_kernel(GArgs a, const __grid_
         const int s = (int)(c % ring);
         if (c >= ring && !tc::wait(empty + s, (uint32_t)(((c / ring) - 1) & 1), err, tmo)) break;
         if (rprod) {
-          mbar_arrive_expect_tx(full + s, (uint32_t)rbytes);
-          tc::tma_load_2d(rring + (size_t)s * a.rstage, &tmR, mc * kGChunk, (int)(tile * a.nt), full + s);
+          unsigned char* st = rring + (size_t)s * a.rstage;
+          mbar_arrive_expect_tx(full + s, (uint32_t)(2 * hbytes));
+          tc::tma_load_2d(st, &tmR, mc * kGChunk, (int)(tile * a.nt), full + s);
+          tc::tma_load_2d(st + hbytes, &tmR, mc * kGChunk + kGBox, (int)(tile * a.nt), full + s);
         } else {
-          mbar_arrive_expect_tx(full + s, (uint32_t)KN * 192);
-          bulk_load(bring + (size_t)s * a.bstage, a.Bg + (size_t)mc * 3 * KN * kGChunk, (uint32_t)KN * 192, full + s);
+          mbar_arrive_expect_tx(full + s, bbytes);
+          bulk_load(bring + (size_t)s * a.bstage, a.Bg + (size_t)mc * 3 * KN * kGChunk, bbytes, full + s);
         }
       }
       // copies still in flight complete before the CTA exits (bounded)
@@ -356,8 +367,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) g_kernel(GArgs a, const __grid_
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t idesc = tc::instr_desc_bf16(128, KN);
+      const uint32_t id2 = tc::instr_desc_bf16(128, 2 * KN), id1 = tc::instr_desc_bf16(128, KN);
       const uint64_t bdesc_ring = tc::smem_desc(smem_u32(bring), 128u, (uint32_t)kGChunk * 16u);
+      const uint32_t pterm = (uint32_t)(KN * kGChunk * 2);    // bytes of one term of the B chunk
       int64_t c = 0;
       for (; c < total; ++c) {
         const int64_t ti = c / a.mchunks;
@@ -372,21 +384,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) g_kernel(GArgs a, const __grid_
         if (gfirst && gi >= 2 && !tc::wait(bars + G_ACCEMPTY + x, (uint32_t)(((gi >> 1) - 1) & 1), err, tmo)) break;
         tc::fence_after();
         const uint64_t bd0 = desc_add(bdesc_ring, (uint32_t)((size_t)s * a.bstage));
-        const uint32_t pterm = (uint32_t)(KN * kGChunk * 2);    // bytes of one term of the B chunk
+        const uint32_t a0 = tmem + staging(b);
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          if (h * 128 < a.nt) {
-            const uint32_t d = tmem + accum(x, h);
-            const uint32_t a0 = tmem + staging(b, h);
-#pragma unroll
-            for (int pr = 0; pr < kProds; ++pr) {
-#pragma unroll
-              for (int kk = 0; kk < kGChunk / 16; ++kk)
-                tc::mma_bf16_tmem_a(d, a0 + (uint32_t)(16 * prod_a(pr) + 8 * kk),
-                                    desc_add(bd0, (uint32_t)(prod_b(pr) * pterm + kk * 256)), idesc,
-                                    (!gfirst || pr > 0 || kk > 0) ? 1u : 0u);
-            }
-          }
+        for (int kk = 0; kk < kGChunk / 16; ++kk) {
+          const uint64_t b01 = desc_add(bd0, (uint32_t)(kk * 256));              // [B0 B1], N = 2KN
+          const uint64_t b2 = desc_add(bd0, (uint32_t)(2 * pterm + kk * 256));    // B2
+          const uint32_t ak = (uint32_t)(8 * kk);
+          tc::mma_bf16_tmem_a(tmem + accum(x, 0), a0 + ak, b01, id2, (!gfirst || kk > 0) ? 1u : 0u);
+          tc::mma_bf16_tmem_a(tmem + accum(x, 0), a0 + 32u + ak, b01, id2, 1u);
+          tc::mma_bf16_tmem_a(tmem + accum(x, 1), a0 + ak, b2, id1, 1u);
+          tc::mma_bf16_tmem_a(tmem + accum(x, 1), a0 + 64u + ak, b01, id1, 1u);   // B0 alone: N = KN
         }
         tc::mma_commit(bars + G_BEMPTY + s);
         tc::mma_commit(bars + G_SFREE + b);
@@ -395,10 +402,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) g_kernel(GArgs a, const __grid_
       shared_flags[0] = (int)std::min<int64_t>(c, 1 << 30);
     }
   } else if (warp >= 4) {
+    // Eight warps: warp w holds TMEM lane quarter w % 4 (tile columns
+    // 32 (w % 4) ..) and rows 32 rh .. 32 rh + 31 of each chunk (rh = (w - 4) / 4,
+    // the chunk's tensor copy rh); in a drain it adds the g entries
+    // k = rh KN/2 .. of its columns.
     const int sw = warp - 4;
-    const int quarter = warp & 3, half = sw >> 2;
-    const int jl = half * 128 + quarter * 32 + lane;     // column within the tile (TMEM lane jl % 128)
+    const int quarter = warp & 3, rh = sw >> 2;
+    const int jl = quarter * 32 + lane;                  // column within the tile (TMEM lane)
     const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+    const int kh = KN / 2;
     bool ok = true;
     int drained = 0;    // groups of the current tile added into the sums
     // Add group gl of tile ti (accumulator set gi & 1) into this column's sums.
@@ -410,13 +422,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) g_kernel(GArgs a, const __grid_
       good = __all_sync(0xffffffffu, good);
       if (!good) return false;
       tc::fence_after();
-      for (int k0 = 0; k0 < KN; k0 += 16) {
-        float v[16];
-        tc::tmem_ld<16>(tmem + lane_base + accum(x, half) + (uint32_t)k0, v);
+      for (int k0 = rh * kh; k0 < (rh + 1) * kh; k0 += 8) {     // kh is a multiple of 8
+        float v0[8], v1[8];
+        tc::tmem_ld<8>(tmem + lane_base + accum(x, 0) + (uint32_t)k0, v0);
+        tc::tmem_ld<8>(tmem + lane_base + accum(x, 1) + (uint32_t)k0, v1);
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
-          float* q = gsum + (size_t)(k0 + u) * 256 + jl;
-          *q = gl == 0 ? v[u] : *q + v[u];
+        for (int u = 0; u < 8; ++u) {
+          const float t = v0[u] + v1[u];
+          float* q = gsum + (size_t)(k0 + u) * 128 + jl;
+          *q = gl == 0 ? t : *q + t;
         }
       }
       tc::fence_before();
@@ -433,15 +447,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) g_kernel(GArgs a, const __grid_
       ok = tc::wait(bars + G_RFULL + s, (uint32_t)((c / a.rs) & 1), err, tmo);
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) break;
-      // Row jl of the swizzled tile: logical 16-byte chunk q sits at chunk q ^ (jl % 8).
+      // Column jl of tensor copy rh (128 bytes, swizzled): logical 16-byte
+      // piece q sits at piece q ^ (jl % 8).
       float4 v[8];
-      const unsigned char* row = rring + (size_t)s * a.rstage + (size_t)jl * 128;
+      const unsigned char* colp = rring + (size_t)s * a.rstage + (size_t)rh * hbytes + (size_t)jl * 128;
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (jl < a.nt) v[q] = *reinterpret_cast<const float4*>(row + ((q ^ (jl & 7)) << 4));
+        if (jl < a.nt) v[q] = *reinterpret_cast<const float4*>(colp + ((q ^ (jl & 7)) << 4));
       }
-      // the chunk is in registers: its buffer goes back to the producer
+      // the rows are in registers: the buffer goes back to the producer
       __syncwarp();
       if (lane == 0) mbar_arrive(bars + G_REMPTY + s);
       uint32_t t0[16], t1[16], t2[16];
@@ -454,10 +469,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) g_kernel(GArgs a, const __grid_
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) break;
       tc::fence_after();
-      const uint32_t col = staging(b, half);
+      const uint32_t col = staging(b) + (uint32_t)(16 * rh);
       tc::tmem_st_u16(tmem + lane_base + col, t0);
-      tc::tmem_st_u16(tmem + lane_base + col + 16, t1);
-      tc::tmem_st_u16(tmem + lane_base + col + 32, t2);
+      tc::tmem_st_u16(tmem + lane_base + col + 32, t1);
+      tc::tmem_st_u16(tmem + lane_base + col + 64, t2);
       tc::tmem_st_wait();
       tc::fence_before();
       __syncwarp();
@@ -472,7 +487,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) g_kernel(GArgs a, const __grid_
           const int64_t j = tile * a.nt + jl;
           if (jl < a.nt && j < a.N) {
             float* gj = a.g + (size_t)j * a.K;
-            for (int k = 0; k < a.K; ++k) gj[k] = gsum[(size_t)k * 256 + jl];
+            for (int k = rh * kh; k < min(a.K, (rh + 1) * kh); ++k) gj[k] = gsum[(size_t)k * 128 + jl];
           }
           drained = 0;
         }
@@ -765,7 +780,7 @@ struct UArgs {
 //   ACCFULL (1), ACCEMPTY (8)         the accumulator of Y Z (one, three ranges)
 //   EREADY[x] (8), EFREE[x] (1)       E' buffers (three terms each) in TMEM
 //   YREADY (8)                        the Y row block of the next unit is in TMEM
-//   WFULL[w] (1), WEMPTY[w] (8)       W sets of alternate groups of tiles
+//   WFULL (1), WEMPTY (8)             the W accumulator (one, two ranges)
 //   DRAIN (1)
 constexpr int kURing = kURingMax;
 enum { U_RFULL = 0, U_REMPTY = kURing, U_EPIDONE = 2 * kURing, U_ZFULL = 3 * kURing, U_ZEMPTY = 3 * kURing + 4,
@@ -773,10 +788,10 @@ enum { U_RFULL = 0, U_REMPTY = kURing, U_EPIDONE = 2 * kURing, U_ZFULL = 3 * kUR
        U_YREADY = U_EFREE + 2, U_WFULL = U_YREADY + 1, U_WEMPTY = U_WFULL + 2, U_DRAIN = U_WEMPTY + 2, U_NBARS };
 
 // Tiles of one W accumulation group: the tensor cores sum a group's
-// contributions to the unit's W rows in one of two TMEM sets, and the
-// epilogue warps add each group's total in float32 (round to nearest) in
-// shared memory one tile later, which keeps the accumulator chains short over
-// the unit's many columns without stalling the pipeline.
+// contributions to the unit's W rows in TMEM, and the epilogue warps add each
+// group's total in float32 (round to nearest) in shared memory at the next
+// group's first tile, which keeps the accumulator chains short over the
+// unit's many columns; the next group's first W products wait for that add.
 constexpr int kWGroup = 8;
 
 __device__ __forceinline__ void unit_tiles(const UArgs& a, int u, int& rb, int64_t& t0, int64_t& t1) {
@@ -806,19 +821,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) update_kernel(UArgs a, const __
   const size_t cpart = (size_t)KN * nu * 2;       // bytes of one term of the C'^T tile
   const size_t zbytes = 3 * zpart, cbytes = 3 * cpart;
   // TMEM columns: the accumulator of Y Z in three ranges of nu columns,
-  // two E' buffers (three terms of nu/2 columns each), two W sets, and the
-  // three terms of the Y row block.  With the terms of the Z tile stacked
-  // along N (they lie one after another in the tile), one MMA per term of Y
-  // forms several products:
+  // two E' buffers (three terms of nu/2 columns each), the W accumulator in
+  // two ranges of KN columns, and the three terms of the Y row block.  With
+  // the terms of the Z tile stacked along N (they lie one after another in the
+  // tile), one MMA per term of Y forms several products:
   //   Y0 [Z0 Z1 Z2] -> ranges 0, 1, 2;  Y1 [Z0 Z1] -> ranges 1, 2;  Y2 Z0 -> range 2,
   // so range 0 holds Y0 Z0, range 1 Y0 Z1 + Y1 Z0, range 2 the 2^-16 terms
   // Y0 Z2 + Y1 Z1 + Y2 Z0, and Y Z = range 0 + (range 1 + range 2).  A
   // tcgen05.mma of M = 128 costs about the same for every N up to 128, so
   // three MMAs of N = 3nu, 2nu, nu per K step do the work of six of N = nu.
+  // W = E' C'^T likewise, with the terms of C'^T stacked two at a time:
+  //   E0 [C0 C1] and E1 [C0 C1] -> ranges 0, 1;  E0 C2 and E2 C0 -> range 1,
+  // so range 0 holds E0 C0 + E1 C0 and range 1 the other four products, and
+  // W = range 0 + range 1: four MMAs of N = 2KN, 2KN, KN, KN per K step
+  // instead of six of N = KN.
   const uint32_t W0 = 6 * nu, Y0 = 6 * nu + 2 * KN;
   auto ACC = [&](int r) { return (uint32_t)(r * nu); };
   auto EP = [&](int x, int p) { return (uint32_t)(3 * nu + x * (3 * nu / 2) + p * (nu / 2)); };
-  auto WS = [&](int w) { return W0 + (uint32_t)(w * KN); };
+  auto WS = [&](int r) { return W0 + (uint32_t)(r * KN); };
   auto YP = [&](int p) { return Y0 + (uint32_t)(p * (Z16 / 2)); };
 
   if (threadIdx.x == 0) {
@@ -826,7 +846,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) update_kernel(UArgs a, const __
     for (int i = 0; i < U_NBARS; ++i) {
       const bool per_warp = (i >= U_EPIDONE && i < U_EPIDONE + kURing) || (i >= U_ACCEMPTY && i < U_ACCEMPTY + 2) ||
                             (i >= U_EREADY && i < U_EREADY + 2) || i == U_YREADY ||
-                            (i >= U_WEMPTY && i < U_WEMPTY + 2);
+                            i == U_WEMPTY;
       mbar_init(bars + i, per_warp ? kWorkWarps : 1);
     }
   }
@@ -880,36 +900,39 @@ __global__ void __launch_bounds__(kTcThreads, 1) update_kernel(UArgs a, const __
     // ------------------------------------------------------------- MMA issue
     if (lane == 0) {
       const uint32_t iU3 = tc::instr_desc_bf16(128, 3 * nu), iU2 = tc::instr_desc_bf16(128, 2 * nu);
-      const uint32_t iU1 = tc::instr_desc_bf16(128, nu), iW = tc::instr_desc_bf16(128, KN);
+      const uint32_t iU1 = tc::instr_desc_bf16(128, nu), iW1 = tc::instr_desc_bf16(128, KN);
+      const uint32_t iW2 = tc::instr_desc_bf16(128, 2 * KN);
       const uint64_t zdesc_ring = tc::smem_desc(smem_u32(zring), 128u, (uint32_t)Z16 * 16u);
       const uint64_t cdesc_ring = tc::smem_desc(smem_u32(zring), 128u, (uint32_t)nu * 16u);
       int64_t i = 0;
       bool ok = true;
-      int64_t wg = 0;     // W groups started so far (set wg & 1)
+      int64_t wg = 0;     // W groups started so far
       // W(i): E'(i) (three terms, TMEM) times C'^T(i) (three terms, shared)
-      // into the current W set; rel is the tile's place in its unit of n tiles.
+      // into the W accumulator; rel is the tile's place in its unit of n tiles.
+      // A group's first products wait until the previous group has been added
+      // into the sums.
       auto issue_w = [&](int64_t iw, int64_t rel, int64_t n) -> bool {
         const int s = (int)(iw % ZS), x = (int)(iw & 1);
         const bool gfirst = rel % kWGroup == 0;
         const bool glast = rel % kWGroup == kWGroup - 1 || rel == n - 1;
-        const int w = (int)(wg & 1);
         if (!tc::wait(bars + U_EREADY + x, (uint32_t)((iw >> 1) & 1), err, tmo)) return false;
-        if (gfirst && wg >= 2 && !tc::wait(bars + U_WEMPTY + w, (uint32_t)(((wg >> 1) - 1) & 1), err, tmo))
-          return false;
+        if (gfirst && wg >= 1 && !tc::wait(bars + U_WEMPTY, (uint32_t)((wg - 1) & 1), err, tmo)) return false;
         tc::fence_after();
         const uint64_t cd0 = desc_add(cdesc_ring, (uint32_t)((size_t)s * a.zstage + zbytes));
 #pragma unroll
-        for (int pr = 0; pr < kProds; ++pr) {
-#pragma unroll
-          for (int kk = 0; kk < nu / 16; ++kk)
-            tc::mma_bf16_tmem_a(tmem + WS(w), tmem + EP(x, prod_a(pr)) + (uint32_t)kk * 8u,
-                                desc_add(cd0, (uint32_t)(prod_b(pr) * cpart + kk * 256)), iW,
-                                (gfirst && pr == 0 && kk == 0) ? 0u : 1u);
+        for (int kk = 0; kk < nu / 16; ++kk) {
+          const uint64_t c01 = desc_add(cd0, (uint32_t)(kk * 256));              // [C0 C1], N = 2KN
+          const uint64_t c2 = desc_add(cd0, (uint32_t)(2 * cpart + kk * 256));    // C2
+          const uint32_t ak = (uint32_t)kk * 8u;
+          tc::mma_bf16_tmem_a(tmem + WS(0), tmem + EP(x, 0) + ak, c01, iW2, (gfirst && kk == 0) ? 0u : 1u);
+          tc::mma_bf16_tmem_a(tmem + WS(0), tmem + EP(x, 1) + ak, c01, iW2, 1u);
+          tc::mma_bf16_tmem_a(tmem + WS(1), tmem + EP(x, 0) + ak, c2, iW1, 1u);
+          tc::mma_bf16_tmem_a(tmem + WS(1), tmem + EP(x, 2) + ak, c01, iW1, 1u);   // C0 alone: N = KN
         }
         tc::mma_commit(bars + U_EFREE + x);
         tc::mma_commit(bars + U_ZEMPTY + s);
         if (glast) {
-          tc::mma_commit(bars + U_WFULL + w);
+          tc::mma_commit(bars + U_WFULL);
           ++wg;
         }
         return true;
@@ -1014,26 +1037,27 @@ __global__ void __launch_bounds__(kTcThreads, 1) update_kernel(UArgs a, const __
       __syncwarp();
       if (lane == 0) mbar_arrive(bars + U_YREADY);
     };
-    // Add W group wgE (set wgE & 1) into this thread's row sums; the unit's
-    // first group starts them.
+    // Add W group wgE (range 0 + range 1) into this thread's row sums; the
+    // unit's first group starts them.
     auto drain_w = [&](bool first_of_unit) -> bool {
-      const int w = (int)(wgE & 1);
-      bool good = tc::wait(bars + U_WFULL + w, (uint32_t)((wgE >> 1) & 1), err, tmo);
+      bool good = tc::wait(bars + U_WFULL, (uint32_t)(wgE & 1), err, tmo);
       good = __all_sync(0xffffffffu, good);
       if (!good) return false;
       tc::fence_after();
       for (int k0 = 0; k0 < kh; k0 += 8) {
-        float wv[8];
-        tc::tmem_ld<8>(tmem + lane_base + WS(w) + (uint32_t)(h * kh + k0), wv);
+        float w0[8], w1[8];
+        tc::tmem_ld<8>(tmem + lane_base + WS(0) + (uint32_t)(h * kh + k0), w0);
+        tc::tmem_ld<8>(tmem + lane_base + WS(1) + (uint32_t)(h * kh + k0), w1);
 #pragma unroll
         for (int v = 0; v < 8; ++v) {
+          const float wv = w0[v] + w1[v];
           float* q = wsum + (size_t)(h * kh + k0 + v) * 128 + row;
-          *q = first_of_unit ? wv[v] : *q + wv[v];
+          *q = first_of_unit ? wv : *q + wv;
         }
       }
       tc::fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(bars + U_WEMPTY + w);
+      if (lane == 0) mbar_arrive(bars + U_WEMPTY);
       ++wgE;
       return true;
     };
@@ -1399,7 +1423,7 @@ cudaError_t batched_reset(BatchedState* b, float* Y, int ld, int K, double e2, c
 static bool encode_maps(BatchedState* b, const float* R) {
   if (b->mapped_R == R) return true;
   const BPlan& P = b->P;
-  if (!encode_f32_colmajor(&b->tmG, R, P.ld, P.N, P.ld, kGChunk, P.nt, CU_TENSOR_MAP_SWIZZLE_128B) ||
+  if (!encode_f32_colmajor(&b->tmG, R, P.ld, P.N, P.ld, kGBox, P.nt, CU_TENSOR_MAP_SWIZZLE_128B) ||
       !encode_f32_colmajor(&b->tmU, R, P.ld, P.N, P.ld, 128, P.nu, CU_TENSOR_MAP_SWIZZLE_NONE))
     return false;
   b->mapped_R = R;
