@@ -107,13 +107,18 @@ __device__ __forceinline__ uint64_t desc_add(uint64_t d, uint32_t bytes) { retur
 
 // Three bfloat16 terms of v, packed in pairs along K: word w of term p holds
 // elements 2w (low half) and 2w + 1 (high half).
+__device__ __forceinline__ uint32_t cvt_bf16x2(float lo, float hi) {
+  const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);   // one conversion, round to nearest even
+  return *reinterpret_cast<const uint32_t*>(&p);
+}
 __device__ __forceinline__ void split_pair(float v0, float v1, uint32_t& w0, uint32_t& w1, uint32_t& w2) {
-  __nv_bfloat16 a0, a1, a2, b0, b1, b2;
-  tc::split_bf16x3(v0, a0, a1, a2);
-  tc::split_bf16x3(v1, b0, b1, b2);
-  w0 = tc::pack_bf16x2(a0, b0);
-  w1 = tc::pack_bf16x2(a1, b1);
-  w2 = tc::pack_bf16x2(a2, b2);
+  // the same terms as tc::split_bf16x3 of each value (a bfloat16 widens to
+  // float32 by a shift), two values per conversion
+  w0 = cvt_bf16x2(v0, v1);
+  const float r0 = v0 - __uint_as_float(w0 << 16), r1 = v1 - __uint_as_float(w0 & 0xffff0000u);
+  w1 = cvt_bf16x2(r0, r1);
+  const float s0 = r0 - __uint_as_float(w1 << 16), s1 = r1 - __uint_as_float(w1 & 0xffff0000u);
+  w2 = cvt_bf16x2(s0, s1);
 }
 
 __device__ __forceinline__ unsigned char* align1024(unsigned char* p) {
