@@ -77,6 +77,9 @@ namespace {
 constexpr int kMaxK = 64;             // tensor-memory budget of the update pass
 constexpr int kTcThreads = 384;       // warp 0 producer, warp 1 MMA, 2-3 idle, 4-11 split / epilogue
 constexpr int kWorkWarps = 8;
+// The g pass adds four drain warps (12-15) to the eight split warps.
+constexpr int kGThreads = 512;
+constexpr int kGDrainWarps = 4;
 constexpr int kGChunk = 64;           // rows of R_s per g stage (256 bytes of a column)
 constexpr int kGBox = 32;             // rows per tensor copy (128 bytes: the 128-byte swizzle's span)
 constexpr int kGMaxRing = 8;          // most stages of a ring of the g pass
@@ -278,7 +281,7 @@ struct GArgs {
 //   RFULL[r] (1, tx), REMPTY[r] (8)    R chunk ring
 //   BFULL[b] (1, tx), BEMPTY[b] (1)    B chunk ring (commit)
 //   SREADY[x] (8), SFREE[x] (1)        TMEM staging buffers of the split terms
-//   ACCFULL[x] (1), ACCEMPTY[x] (8)    accumulator sets of alternate groups
+//   ACCFULL[x] (1), ACCEMPTY[x] (4)    accumulator sets of alternate groups
 //   DRAIN (1)
 enum { G_RFULL = 0, G_REMPTY = kGMaxRing, G_BFULL = 2 * kGMaxRing, G_BEMPTY = 3 * kGMaxRing,
        G_SREADY = 4 * kGMaxRing, G_SFREE = G_SREADY + 2, G_ACCFULL = G_SFREE + 2, G_ACCEMPTY = G_ACCFULL + 2,
@@ -301,7 +304,7 @@ constexpr int kGGroup = 2;
 // g = range 0 + range 1.  Four MMAs of N = 2KN, 2KN, KN, KN per K step do
 // the work of six of N = KN (an MMA of M = 128 costs about the same for
 // every N up to 128).
-__global__ void __launch_bounds__(kTcThreads, 1) g_kernel(GArgs a, const __grid_constant__ CUtensorMap tmR) {
+__global__ void __launch_bounds__(kGThreads, 1) g_kernel(GArgs a, const __grid_constant__ CUtensorMap tmR) {
   extern __shared__ unsigned char sm_raw[];
   unsigned char* sm = align1024(sm_raw);
   unsigned char* rring = sm;                                                   // R chunks
@@ -317,9 +320,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) g_kernel(GArgs a, const __grid_
   if (threadIdx.x == 0) {
     shared_flags[0] = 0;
     for (int i = 0; i < G_NBARS; ++i) {
-      const bool per_warp = (i >= G_REMPTY && i < G_REMPTY + kGMaxRing) || i == G_SREADY || i == G_SREADY + 1 ||
-                            i == G_ACCEMPTY || i == G_ACCEMPTY + 1;
-      mbar_init(bars + i, per_warp ? kWorkWarps : 1);
+      const bool split = (i >= G_REMPTY && i < G_REMPTY + kGMaxRing) || i == G_SREADY || i == G_SREADY + 1;
+      const bool drain = i == G_ACCEMPTY || i == G_ACCEMPTY + 1;
+      mbar_init(bars + i, split ? kWorkWarps : (drain ? kGDrainWarps : 1));
     }
   }
   fence_mbar_init();
@@ -406,48 +409,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) g_kernel(GArgs a, const __grid_
       }
       shared_flags[0] = (int)std::min<int64_t>(c, 1 << 30);
     }
-  } else if (warp >= 4) {
-    // Eight warps: warp w holds TMEM lane quarter w % 4 (tile columns
-    // 32 (w % 4) ..) and rows 32 rh .. 32 rh + 31 of each chunk (rh = (w - 4) / 4,
-    // the chunk's tensor copy rh); in a drain it adds the g entries
-    // k = rh KN/2 .. of its columns.
-    const int sw = warp - 4;
-    const int quarter = warp & 3, rh = sw >> 2;
+  } else if (warp >= 4 && warp < 12) {
+    // Split warps: warp w holds TMEM lane quarter w % 4 (tile columns
+    // 32 (w % 4) ..) and rows 32 rh .. 32 rh + 31 of each chunk
+    // (rh = (w - 4) / 4, the chunk's tensor copy rh).
+    const int quarter = warp & 3, rh = (warp - 4) >> 2;
     const int jl = quarter * 32 + lane;                  // column within the tile (TMEM lane)
     const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
-    const int kh = KN / 2;
     bool ok = true;
-    int drained = 0;    // groups of the current tile added into the sums
-    // Add group gl of tile ti (accumulator set gi & 1) into this column's sums.
-    auto drain = [&](int64_t ti, int gl) -> bool {
-      if (gl != drained) return true;
-      const int64_t gi = ti * ngroups + gl;
-      const int x = (int)(gi & 1);
-      bool good = tc::wait(bars + G_ACCFULL + x, (uint32_t)((gi >> 1) & 1), err, tmo);
-      good = __all_sync(0xffffffffu, good);
-      if (!good) return false;
-      tc::fence_after();
-      for (int k0 = rh * kh; k0 < (rh + 1) * kh; k0 += 8) {     // kh is a multiple of 8
-        float v0[8], v1[8];
-        tc::tmem_ld<8>(tmem + lane_base + accum(x, 0) + (uint32_t)k0, v0);
-        tc::tmem_ld<8>(tmem + lane_base + accum(x, 1) + (uint32_t)k0, v1);
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const float t = v0[u] + v1[u];
-          float* q = gsum + (size_t)(k0 + u) * 128 + jl;
-          *q = gl == 0 ? t : *q + t;
-        }
-      }
-      tc::fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(bars + G_ACCEMPTY + x);
-      ++drained;
-      return true;
-    };
     for (int64_t c = 0; c < total && ok; ++c) {
-      const int64_t ti = c / a.mchunks;
-      const int mc = (int)(c % a.mchunks);
-      const int64_t tile = blockIdx.x + ti * gridDim.x;
       const int s = (int)(c % a.rs), b = (int)(c & 1);
       ok = tc::wait(bars + G_RFULL + s, (uint32_t)((c / a.rs) & 1), err, tmo);
       ok = __all_sync(0xffffffffu, ok);
@@ -482,20 +452,44 @@ __global__ void __launch_bounds__(kTcThreads, 1) g_kernel(GArgs a, const __grid_
       tc::fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(bars + G_SREADY + b);
-      // Group totals are added one group later (while the next group's MMAs
-      // run, its products long done); the tile's last groups at its end.
-      const int gl = mc / kGGroup, pos = mc % kGGroup;
-      if (pos == 1 && gl >= 1) ok = drain(ti, gl - 1);
-      if (ok && mc == a.mchunks - 1) {
-        while (ok && drained < ngroups) ok = drain(ti, drained);
-        if (ok) {
-          const int64_t j = tile * a.nt + jl;
-          if (jl < a.nt && j < a.N) {
-            float* gj = a.g + (size_t)j * a.K;
-            for (int k = rh * kh; k < min(a.K, (rh + 1) * kh); ++k) gj[k] = gsum[(size_t)k * 128 + jl];
+    }
+  } else if (warp >= 12) {
+    // Drain warps: warp w holds TMEM lane quarter w % 4; it adds each group's
+    // accumulator (range 0 + range 1) into its columns' float32 sums as soon
+    // as the group's products are done, and stores g at each tile's end.
+    const int quarter = warp & 3;
+    const int jl = quarter * 32 + lane;
+    const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+    bool ok = true;
+    for (int64_t ti = 0; ti < ntile && ok; ++ti) {
+      const int64_t tile = blockIdx.x + ti * gridDim.x;
+      for (int gl = 0; gl < ngroups && ok; ++gl) {
+        const int64_t gi = ti * ngroups + gl;
+        const int x = (int)(gi & 1);
+        ok = tc::wait(bars + G_ACCFULL + x, (uint32_t)((gi >> 1) & 1), err, tmo);
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) break;
+        tc::fence_after();
+        for (int k0 = 0; k0 < KN; k0 += 16) {
+          float v0[16], v1[16];
+          tc::tmem_ld2x16(tmem + lane_base + accum(x, 0) + (uint32_t)k0, tmem + lane_base + accum(x, 1) + (uint32_t)k0,
+                          v0, v1);
+#pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            const float t = v0[u] + v1[u];
+            float* q = gsum + (size_t)(k0 + u) * 128 + jl;
+            *q = gl == 0 ? t : *q + t;
           }
-          drained = 0;
         }
+        tc::fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bars + G_ACCEMPTY + x);
+      }
+      if (!ok) break;
+      const int64_t j = tile * a.nt + jl;
+      if (jl < a.nt && j < a.N) {
+        float* gj = a.g + (size_t)j * a.K;
+        for (int k = 0; k < a.K; ++k) gj[k] = gsum[(size_t)k * 128 + jl];
       }
     }
   }
@@ -1463,7 +1457,7 @@ cudaError_t batched_sweep(BatchedState* b, float* R, float* Y, float* C, int ld,
   ga.rstage = P.grstage;
   ga.bstage = P.gbstage;
   ga.timeout_ns = timeout_ns;
-  g_kernel<<<P.ggrid, kTcThreads, P.gsmem, s>>>(ga, b->tmG);
+  g_kernel<<<P.ggrid, kGThreads, P.gsmem, s>>>(ga, b->tmG);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // the K successive c updates per column, with the next pass's operand tiles and V partials

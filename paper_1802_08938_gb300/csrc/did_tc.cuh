@@ -157,6 +157,20 @@ __device__ __forceinline__ void tmem_ld3x16(uint32_t t0, uint32_t t1, uint32_t t
   }
 }
 
+__device__ __forceinline__ void tmem_ld2x16(uint32_t t0, uint32_t t1, float* v0, float* v1) {
+  uint32_t a[16], b[16];
+  tmem_ld16_nowait(t0, a);
+  tmem_ld16_nowait(t1, b);
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  regs_after_wait16(a);
+  regs_after_wait16(b);
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    v0[i] = __uint_as_float(a[i]);
+    v1[i] = __uint_as_float(b[i]);
+  }
+}
+
 // N consecutive float32 columns into this thread's TMEM lane (warp-collective).
 // The stores are asynchronous: tmem_st_wait() completes them, and a following
 // fence_before + mbarrier arrive publishes the values to the MMA thread.
