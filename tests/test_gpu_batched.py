@@ -36,10 +36,12 @@ def run(did, X, B0, C0, sweeps, order, **kw):
         return B, C, ctx.trace(), ctx.residual(), ctx.objective()
 
 
-# Shapes over one and several 128-row blocks and 32/64-column tiles, with
-# ragged tails in both directions, K from 3 to the supported 64.
+# Shapes over one and several 128-row blocks, 64-row chunks and 32/64-column
+# tiles, with ragged tails in both directions, K from 3 to the supported 64
+# (every row-slot count ceil(K/8) = 1..8 of the column solve).
 @pytest.mark.parametrize("M,N,K", [(200, 1000, 10), (37, 53, 3), (784, 700, 16), (2001, 311, 5), (300, 5000, 64),
-                                   (129, 257, 64), (1000, 4099, 50), (5000, 1500, 50)])
+                                   (129, 257, 64), (1000, 4099, 50), (5000, 1500, 50), (333, 777, 29),
+                                   (450, 611, 37), (257, 903, 45), (190, 640, 57)])
 def test_batched_matches_algorithm3(did, M, N, K):
     X, _, _ = W.planted(M, N, K, seed=M + 5 * N, sigma=0.01)
     B0, C0 = W.init_factors(M, N, K, 6)
