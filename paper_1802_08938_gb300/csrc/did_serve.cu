@@ -226,33 +226,27 @@ double sweep_cta_s(const did_server* s, const Req* r) {
   return (double)r->rq.K * (kPassFixedS + pass_bytes / kCtaBytesPerS);
 }
 
-// Split the launch's CTAs among the active requests in proportion to the
-// CTA-seconds their sweeps take, so that their sweeps take about equally long.
+// Split the launch's CTAs among the active requests so that the slowest
+// sweep is as short as possible (a round waits for its slowest instance):
+// every request starts with one CTA, and each further CTA goes to the request
+// whose sweep, at its CTA-seconds / CTAs, would take longest (ties to the
+// lower index).  An instance never gets more CTAs than it has columns.
 std::vector<int> shares(const did_server* s, const std::vector<Req*>& act) {
   const int n = (int)act.size();
   std::vector<int> sh(n, 1);
-  double total = 0.0;
   std::vector<double> w(n);
-  for (int i = 0; i < n; ++i) {
-    w[i] = sweep_cta_s(s, act[i]);
-    total += w[i];
-  }
-  int left = s->grid - n;
-  if (left > 0 && total > 0) {
-    int given = 0;
+  for (int i = 0; i < n; ++i) w[i] = sweep_cta_s(s, act[i]);
+  for (int left = s->grid - n; left > 0; --left) {
+    int best = -1;
+    double tb = -1.0;
     for (int i = 0; i < n; ++i) {
-      const int extra = (int)floor(w[i] / total * left);
-      sh[i] += extra;
-      given += extra;
+      if (sh[i] >= act[i]->rq.N) continue;
+      const double t = w[i] / sh[i];
+      if (t > tb) { tb = t; best = i; }
     }
-    // leftovers to the largest requests
-    std::vector<int> order(n);
-    for (int i = 0; i < n; ++i) order[i] = i;
-    std::sort(order.begin(), order.end(), [&](int a, int b) { return w[a] > w[b]; });
-    for (int t = 0; given < left; ++t, ++given) sh[order[t % n]] += 1;
+    if (best < 0) break;
+    ++sh[best];
   }
-  // an instance never gets more CTAs than it has columns
-  for (int i = 0; i < n; ++i) sh[i] = (int)std::max<int64_t>(1, std::min<int64_t>(sh[i], act[i]->rq.N));
   return sh;
 }
 
