@@ -36,17 +36,23 @@
 // chain of MMA additions drifts: g summed over 5000 rows in one accumulator
 // moved B and C by 4.9e-5 of the float64 result in 20 sweeps.  The g pass
 // therefore drains its accumulator into float32 sums on the CUDA cores every
-// four 32-row chunks, and the update pass its W accumulator every eight
-// tiles, each into a second accumulator set so the MMAs do not wait.
+// 128 rows (two chunks of 64; into a second accumulator set meanwhile, so the
+// MMAs do not wait), and the update pass its W accumulator every eight tiles.
+//
+// The products are small (M = 128, N = 32 to 128), and a tcgen05.mma of
+// M = 128 costs about the same for every N up to 128, so the passes stack the
+// terms of their shared-memory operand along N: one MMA forms several of the
+// six products into adjacent accumulator ranges (three MMAs per K step for
+// the rank-2K update, four for g and W; see the kernels).
 //
 // Kernels of one sweep (K <= 64):
-//   prep_gb     B -> bfloat16 x3 tiles of 32 rows for the g pass (1 MB at K = 50)
-//   g_kernel    tcgen05: g^T = R_s^T B over column tiles of up to 256 columns.
-//               R_s arrives by 2-D TMA (128-byte swizzle) in chunks of 32 rows;
+//   prep_gb     B -> bfloat16 x3 tiles of 64 rows for the g pass (2 MB at K = 50)
+//   g_kernel    tcgen05: g^T = R_s^T B over column tiles of up to 128 columns.
+//               R_s arrives by 2-D TMA (128-byte swizzle) in chunks of 64 rows;
 //               eight warps split each chunk into its three bfloat16 terms in
-//               tensor memory (the A operand), and one thread issues the six
-//               products.  One read of R_s.
-//   solve_c     per column: g_j - (B^T D) c_j, the K successive c updates,
+//               tensor memory (the A operand), one thread issues the products,
+//               and four warps add the accumulator groups.  One read of R_s.
+//   solve_c     per column (eight lanes each): g_j - (B^T D) c_j, the K successive c updates,
 //               C', the operand tiles [C_old; dl] and C'^T (bfloat16 x3) of
 //               the next pass, and per-block partials of V = C' C'^T.
 //   update      tcgen05, persistent over (128-row block, column range) units:
@@ -188,7 +194,7 @@ bool make_plan(int ld, int64_t N, int K, BPlan* p) {
   }
   // update pass: 64-column tiles where tensor memory holds them, else 32
   // (columns: the accumulator of three ranges, two E' buffers of three terms,
-  // two W sets, three Y terms)
+  // the W accumulator of two ranges, three Y terms)
   auto tmem_cols = [&](int nu) { return 3 * nu + 3 * nu + 2 * P.KN + 3 * P.Z16 / 2; };
   P.nu = tmem_cols(64) <= (int)kTmemCols ? 64 : 32;
   if (tmem_cols(P.nu) > (int)kTmemCols) return false;

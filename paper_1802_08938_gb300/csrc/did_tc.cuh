@@ -6,11 +6,12 @@
 //   - Shared-memory operands are in the no-swizzle K-major core-matrix layout:
 //     a core matrix is 8 rows x 16 bytes; core matrices adjacent along K are
 //     128 bytes apart (LBO), adjacent along M/N are Kp*E*8 bytes apart (SBO)
-//     for a contraction length Kp of E-byte elements.  One tf32 MMA consumes
-//     32 bytes of K (two core matrices), so its start address advances by 256
-//     bytes per K step.
-//   - An A operand held in tensor memory (TMEM) has row i in lane i and one
-//     32-bit element per column; one tf32 MMA reads 8 consecutive columns.
+//     for a contraction length Kp of E-byte elements.  One bfloat16 MMA
+//     (kind::f16) consumes 16 elements of K, 32 bytes (two core matrices), so
+//     its start address advances by 256 bytes per K step.
+//   - An A operand held in tensor memory (TMEM) has row i in lane i and two
+//     bfloat16 elements per 32-bit column (the even K index in the low half);
+//     one MMA reads 8 consecutive columns.
 //   - A warp reads or writes only its own quarter of the 128 TMEM lanes
 //     (lanes 32 (warp % 4) ..), addressed as (lane << 16) | column.
 #pragma once
@@ -44,10 +45,6 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
 __host__ __device__ constexpr uint32_t instr_desc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
-// kind::tf32: the same fields with A and B of format TF32 (value 2).
-__host__ __device__ constexpr uint32_t instr_desc_tf32(int M, int N) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
 
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
@@ -67,25 +64,6 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-// D (TMEM) (+)= A (TMEM, 128 lanes x 8 columns from a_tmem) x B (shared memory).
-__device__ __forceinline__ void mma_tf32_tmem_a(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
-                                                uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
 // Arrive once on an mbarrier when every MMA this thread issued so far is done.
@@ -171,31 +149,9 @@ __device__ __forceinline__ void tmem_ld2x16(uint32_t t0, uint32_t t1, float* v0,
   }
 }
 
-// N consecutive float32 columns into this thread's TMEM lane (warp-collective).
-// The stores are asynchronous: tmem_st_wait() completes them, and a following
-// fence_before + mbarrier arrive publishes the values to the MMA thread.
-template <int N>
-__device__ __forceinline__ void tmem_st(uint32_t taddr, const float* v);
-template <>
-__device__ __forceinline__ void tmem_st<8>(uint32_t taddr, const float* v) {
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
-               "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
-               "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
-               "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
-               : "memory");
-}
-template <>
-__device__ __forceinline__ void tmem_st<16>(uint32_t taddr, const float* v) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
-          taddr),
-      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
-      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
-      "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])),
-      "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])),
-      "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
-      : "memory");
-}
+// TMEM stores are asynchronous: tmem_st_wait() completes them, and a
+// following fence_before + mbarrier arrive publishes the values to the MMA
+// thread.
 __device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // Bounded mbarrier wait used by every role.  A phase that has completed
@@ -243,17 +199,6 @@ __device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bu
 // Wait until this thread's bulk groups are complete (writes visible).
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
-// Split of a float32 value for TF32x3 products: hi is v rounded to TF32's 11
-// significand bits (to nearest, ties away from zero: add half a TF32 ulp to
-// the magnitude bits and clear the 13 low bits; a carry into the exponent is
-// the correct rounding) and lo = v - hi, exact in float32 and at most half a
-// TF32 ulp of v.  The tensor core reads lo as TF32 (its 13 low bits dropped),
-// so the split keeps about 21 significand bits of v.
-__device__ __forceinline__ void split_tf32(float v, float& hi, float& lo) {
-  hi = __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xFFFFE000u);
-  lo = v - hi;
-}
-
 // Split of a float32 value into three bfloat16 terms, each the round-to-
 // nearest of what the previous ones left (the remainders are exact in
 // float32): v = p0 + p1 + p2 + r with |r| <= 2^-27 |v| (three 8-bit
@@ -266,11 +211,6 @@ __device__ __forceinline__ void split_bf16x3(float v, __nv_bfloat16& p0, __nv_bf
   p1 = __float2bfloat16_rn(r1);
   const float r2 = r1 - __bfloat162float(p1);
   p2 = __float2bfloat16_rn(r2);
-}
-__device__ __forceinline__ uint32_t bf16_bits(__nv_bfloat16 x) { return (uint32_t)__bfloat16_as_ushort(x); }
-// Two bfloat16 values in one 32-bit word, the first (even K index) in the low half.
-__device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 even, __nv_bfloat16 odd) {
-  return bf16_bits(even) | (bf16_bits(odd) << 16);
 }
 
 // 8 or 16 32-bit words into this thread's TMEM lane (warp-collective).
