@@ -90,7 +90,9 @@ typedef struct {
     const float* B_init;    /* optional start point, host or device, M x K column-major; NULL = seeded */
     const float* C_init;    /* optional start point, host or device, K x N row-major; NULL = seeded */
     void* stream;           /* cudaStream_t to order all work on; NULL = legacy default stream */
-    uint64_t timeout_ns;    /* limit of every device-side grid wait; 0 = 4 s */
+    uint64_t timeout_ns;    /* limit of every device-side wait; 0 = 4 s; values below
+                               10 ms are raised to 10 ms (a wait also covers the
+                               CTA's own copies and tensor-core work) */
     int32_t debug_barrier_extra; /* test hook: arrivals a grid wait expects beyond the grid (0 in use) */
     int32_t flags;          /* DID_FLAG_* bits */
     /* Inner repeats per sweep (DID_ORDER_DID_BATCHED only; 0 means 1): the C

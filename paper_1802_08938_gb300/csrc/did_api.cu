@@ -18,6 +18,10 @@ namespace {
 
 constexpr int kMaxSweepsPerLaunch = 1024;
 constexpr uint64_t kDefaultTimeoutNs = 4000000000ull;
+// Every device wait also covers this CTA's own copies and tensor-core work,
+// which finish in microseconds; a limit below 10 ms is raised to 10 ms so that
+// a wait never gives up on them.
+constexpr uint64_t kMinTimeoutNs = 10000000ull;
 
 }  // namespace
 
@@ -77,6 +81,13 @@ struct did_ctx {
   std::vector<void*> dev_allocs;
   std::vector<void*> host_allocs;
 };
+
+// The limit of every device wait of a context: the caller's, else 4 s, and
+// at least kMinTimeoutNs.
+static uint64_t wait_limit_ns(const did_ctx* c) {
+  const uint64_t t = c->opt.timeout_ns ? c->opt.timeout_ns : kDefaultTimeoutNs;
+  return t < kMinTimeoutNs ? kMinTimeoutNs : t;
+}
 
 namespace {
 
@@ -231,7 +242,7 @@ did_status refresh_tc(did_ctx* c, double* f) {
   DID_CUDA(c, cudaEventRecord(c->ev0, c->stream));
   DID_CUDA(c, did::launch_refresh_tc(c->X, c->R, c->B, c->C, (int)c->M, c->ld, c->N, c->K, c->tc_ws, c->tc_part,
                                      fuse ? c->P : nullptr, fuse ? c->CCp : nullptr, c->tc_err,
-                                     c->opt.timeout_ns ? c->opt.timeout_ns : kDefaultTimeoutNs, c->stream,
+                                     wait_limit_ns(c), c->stream,
                                      !c->bf16));
   DID_CUDA(c, cudaEventRecord(c->ev1, c->stream));
   DID_CUDA(c, cudaMemcpyAsync(part.data(), c->tc_part, sizeof(double) * G, cudaMemcpyDeviceToHost, c->stream));
@@ -314,7 +325,7 @@ did_status launch_sweeps(did_ctx* c, int n, int stop_rule, double tol, int* done
   a.tol = tol;
   a.order = c->opt.order;
   a.bar_extra = c->opt.debug_barrier_extra;
-  a.timeout_ns = c->opt.timeout_ns ? c->opt.timeout_ns : kDefaultTimeoutNs;
+  a.timeout_ns = wait_limit_ns(c);
   a.tstamp = c->tstamp;
   a.tstamp_cap = c->tstamp_cap;
   c->tstamp_n = c->tstamp ? (int)std::min<int64_t>((int64_t)n * c->K, c->tstamp_cap) : 0;
@@ -375,7 +386,7 @@ did_status run_batched(did_ctx* c, int64_t max_sweeps, int stop_rule, double tol
     }
     const int chunk = chunk_size(c, max_sweeps - *done_total);
     const int n = stop_rule ? 1 : chunk;     // with a stopping rule: one sweep per check
-    const uint64_t tmo = c->opt.timeout_ns ? c->opt.timeout_ns : kDefaultTimeoutNs;
+    const uint64_t tmo = wait_limit_ns(c);
     int* err = did::batched_error_word(c->batched);
     DID_CUDA(c, cudaEventRecord(c->ev0, c->stream));
     for (int s = 0; s < n; ++s)

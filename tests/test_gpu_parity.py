@@ -260,6 +260,22 @@ def test_barrier_timeout_is_reported_and_context_survives(did):
         assert len(ok.trace()) == 3
 
 
+def test_tiny_wait_limit_is_raised(did):
+    """A wait limit of 1 ns is raised to the 10 ms floor, so the waits for a
+    CTA's own copies and tensor-core work never give up: the sweeps (with a
+    tensor-core refresh, and in the batched order) equal those of the default
+    limit bit for bit."""
+    X, M, N, K = W.make("planted_uniform_200x1000_k10", seed=9, M=300, N=900, K=8)
+    Xc = np.ascontiguousarray(X.T)
+    for order in (did.DID_ORDER_INTERLEAVED, did.DID_ORDER_DID_BATCHED):
+        out = []
+        for t in (1, 0):
+            with did.Context(Xc, M, N, K, seed=9, order=order, refresh_every=2, timeout_ns=t) as ctx:
+                ctx.sweep(4)
+                out.append(ctx.factors())
+        assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
 def test_contexts_of_different_sizes_interleave(did):
     """Two live contexts whose plans share a kernel variant but differ in shared
     memory (M = 200 and M = 216, ld 208 and 224) sweep alternately."""
