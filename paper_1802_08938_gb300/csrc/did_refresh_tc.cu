@@ -58,6 +58,7 @@ constexpr int kTileN = 64;          // columns per tile (MMA N)
 constexpr int kMaxKp = 128;         // K padded to a multiple of 16, at most 128 (bfloat16 residual)
 constexpr int kMaxKpF32 = 64;       // three-term operands take 1.5x the shared memory
 constexpr int kMaxXBuf = 4;         // X tile ring
+constexpr int kMaxCBuf = 4;         // C-factor tile ring
 constexpr int kTmemCols = 128;      // two accumulators of kTileN columns
 
 struct TcArgs {
@@ -67,28 +68,31 @@ struct TcArgs {
   const void* Bhl;           // [col tiles][terms][64 cols x Kp] tiled C factor
   double* part;              // [grid] sum of R^2 per CTA
   const float* c1;           // row 1 of C (N floats), or null: no partials
-  float* P1;                 // [2 grid][ld] partials of R c_1^T (row 2 cta + column half)
+  float* P1;                 // [2 grid][ld] partials of R c_1^T (row 2 cta + column half), zeroed by the host
   double* CC1;               // [2 grid] partials of ||c_1||^2
   int* err;                  // error word
   int M, ld, Kp;
   int xbufs;                 // X tile buffers (2..kMaxXBuf)
+  int cbufs;                 // C-factor tile buffers (2..kMaxCBuf)
   int64_t N;
   int row_blocks;            // ceil(ld / 128)
   int64_t col_tiles;         // ceil(N / 64)
+  int Q;                     // column ranges per row block: units = row_blocks * Q
   uint64_t timeout_ns;
 };
 
-// Shared memory plan (bytes) for NT-term bfloat16 operands and XB X buffers.
+// Shared memory plan (bytes) for NT-term bfloat16 operands, XB X buffers and
+// CB C-factor buffers.
 struct TcSmem {
-  size_t A, B, X, bars, tmem_slot, red, steps, total;
+  size_t A, C, X, bars, tmem_slot, red, steps, total;
 };
-__host__ __device__ __forceinline__ TcSmem tc_smem(int Kp, int NT, int XB) {
+__host__ __device__ __forceinline__ TcSmem tc_smem(int Kp, int NT, int XB, int CB) {
   TcSmem L;
   size_t o = 0;
-  L.A = o;    o += (size_t)2 * NT * kTileM * Kp * 2;     // two buffers of the B-factor row block
-  L.B = o;    o += (size_t)NT * kTileN * Kp * 2;         // the C-factor column tile
-  L.X = o;    o += (size_t)XB * kTileN * kTileM * 4;     // X tiles [64 cols][128 rows]
-  L.bars = o; o += 24 * sizeof(uint64_t);
+  L.A = o;    o += (size_t)NT * kTileM * Kp * 2;          // the unit's B-factor row block
+  L.C = o;    o += (size_t)CB * NT * kTileN * Kp * 2;     // C-factor column tiles
+  L.X = o;    o += (size_t)XB * kTileN * kTileM * 4;      // X tiles [64 cols][128 rows]
+  L.bars = o; o += 32 * sizeof(uint64_t);
   L.tmem_slot = o; o += 16;
   L.red = o;  o += 8 * sizeof(double);
   L.steps = o; o += 16;
@@ -98,16 +102,27 @@ __host__ __device__ __forceinline__ TcSmem tc_smem(int Kp, int NT, int XB) {
 
 // Barrier slots.
 enum {
-  BAR_B_FULL = 0,     // C-factor tile landed
-  BAR_A_FULL = 1,     // 1, 2: B-factor row block buffers landed
-  BAR_A_EMPTY = 3,    // 3, 4: MMAs of a step done reading its A buffer (and B)
-  BAR_ACC_FULL = 5,   // 5, 6: accumulator ready (tcgen05.commit)
-  BAR_ACC_EMPTY = 7,  // 7, 8: epilogue done reading an accumulator (one arrival per epilogue warp)
-  BAR_X_FULL = 9,     // 9..12: X tile buffers landed
-  BAR_X_EMPTY = 13,   // 13..16: the R tile stored from an X buffer has been read out
-  BAR_EPI_DONE = 17,  // 17..20: a tile of R is complete in an X buffer (one arrival per epilogue warp)
-  BAR_COUNT = 21
+  BAR_A_FULL = 0,     // the unit's B-factor block landed
+  BAR_A_EMPTY = 1,    // the unit's MMAs are done with it (tcgen05.commit)
+  BAR_C_FULL = 2,     // 2..5: C-factor tile buffers landed
+  BAR_C_EMPTY = 6,    // 6..9: MMAs of a step done reading its C buffer
+  BAR_ACC_FULL = 10,  // 10, 11: accumulator ready (tcgen05.commit)
+  BAR_ACC_EMPTY = 12, // 12, 13: epilogue done reading an accumulator (one arrival per epilogue warp)
+  BAR_X_FULL = 14,    // 14..17: X tile buffers landed
+  BAR_X_EMPTY = 18,   // 18..21: the R tile stored from an X buffer has been read out
+  BAR_EPI_DONE = 22,  // 22..25: a tile of R is complete in an X buffer (one arrival per epilogue warp)
+  BAR_DRAIN = 26,     // every MMA issued is done (before TMEM is freed)
+  BAR_COUNT = 27
 };
+
+// Unit u of the work: row block rb and the column tiles [t0, t1) of range
+// u / row_blocks.  The CTA takes units blockIdx.x, blockIdx.x + grid, ...
+__device__ __forceinline__ void rt_unit(const TcArgs& a, int64_t u, int& rb, int64_t& t0, int64_t& t1) {
+  rb = (int)(u % a.row_blocks);
+  const int64_t q = u / a.row_blocks;
+  t0 = q * a.col_tiles / a.Q;
+  t1 = (q + 1) * a.col_tiles / a.Q;
+}
 
 // F32: a float32 residual from BF16x6 products; otherwise a bfloat16 residual from BF16x3.
 template <bool F32>
@@ -117,29 +132,29 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a, con
   constexpr int NPROD = F32 ? 6 : 3;              // products p_i q_j with i + j <= NT - 1
   constexpr int KSTEP = 16;                       // K per MMA (32 bytes)
   extern __shared__ __align__(1024) unsigned char sm[];
-  const int XB = a.xbufs;
-  const TcSmem L = tc_smem(a.Kp, NT, XB);
+  const int XB = a.xbufs, CB = a.cbufs;
+  const TcSmem L = tc_smem(a.Kp, NT, XB, CB);
   unsigned char* sA = sm + L.A;
-  unsigned char* sB = sm + L.B;
+  unsigned char* sC = sm + L.C;
   float* sX = reinterpret_cast<float*>(sm + L.X);
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + L.bars);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + L.tmem_slot);
   double* red = reinterpret_cast<double*>(sm + L.red);
-  int* mma_steps = reinterpret_cast<int*>(sm + L.steps);   // steps whose MMAs were committed
+  int* mma_steps = reinterpret_cast<int*>(sm + L.steps);   // [0] steps whose MMAs were issued, [1] epilogue failure
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int Kp = a.Kp;
   const uint32_t a_bytes = (uint32_t)NT * kTileM * Kp * 2;
-  const uint32_t b_bytes = (uint32_t)NT * kTileN * Kp * 2;
+  const uint32_t c_bytes = (uint32_t)NT * kTileN * Kp * 2;
   const uint32_t a_split = (uint32_t)kTileM * Kp * 2;     // bytes of one term of the A tile
-  const uint32_t b_split = (uint32_t)kTileN * Kp * 2;
+  const uint32_t c_split = (uint32_t)kTileN * Kp * 2;
 
   if (threadIdx.x == 0) {
     mma_steps[0] = 0;
-    mma_steps[1] = 0;     // epilogue failure flag
+    mma_steps[1] = 0;
     for (int i = 0; i < BAR_COUNT; ++i) {
-      const bool per_warp =
-          i == BAR_ACC_EMPTY || i == BAR_ACC_EMPTY + 1 || (i >= BAR_EPI_DONE && i < BAR_EPI_DONE + kMaxXBuf);
+      const bool per_warp = i == BAR_ACC_EMPTY || i == BAR_ACC_EMPTY + 1 ||
+                            (i >= BAR_EPI_DONE && i < BAR_EPI_DONE + kMaxXBuf);
       mbar_init(bars + i, per_warp ? kEpiWarps : 1);
     }
   }
@@ -150,54 +165,66 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a, con
   tc::fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  // The CTA's work list: column tiles t = blockIdx.x + i*grid, each with all
-  // row blocks.  Step s enumerates (tile, row block) pairs in that order.
-  const int64_t ntile_cta = a.col_tiles > blockIdx.x ? (a.col_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-  const int64_t nsteps = ntile_cta * a.row_blocks;
+  // The CTA's work: units blockIdx.x + i * grid; a unit is one row block of
+  // the B factor (loaded once) against a range of column tiles.  Step s
+  // enumerates the CTA's (unit, column tile) pairs in order.
+  const int64_t nunits = (int64_t)a.row_blocks * a.Q;
   int* err = a.err;
   const uint64_t tmo = a.timeout_ns;
 
   if (warp == 0) {
-    // ------------------------------------------------------------ producer
+    // ------------------------------------------------- operand producer
+    // The unit's B-factor block once the previous unit's MMAs are done with
+    // it; the C-factor tile of every step into a ring of CB buffers.
     if (lane == 0) {
-      for (int64_t s = 0; s < nsteps; ++s) {
-        const int64_t ti = s / a.row_blocks;
-        const int rb = (int)(s % a.row_blocks);
-        const int64_t tile = blockIdx.x + ti * gridDim.x;
-        // A_EMPTY + (t & 1) completes once per use of buffer t & 1: for step t
-        // its phase parity is (t >> 1) & 1.
-        if (rb == 0 && s > 0) {
-          // the previous tile's MMAs (all of them: commits complete in order)
-          // must be done with the C-factor buffer
-          if (!tc::wait(bars + BAR_A_EMPTY + ((s - 1) & 1), (uint32_t)(((s - 1) >> 1) & 1), err, tmo)) break;
+      int64_t s = 0, ui = 0;
+      bool ok = true;
+      for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x, ++ui) {
+        int rb;
+        int64_t t0, t1;
+        rt_unit(a, u, rb, t0, t1);
+        if (ui > 0 && !tc::wait(bars + BAR_A_EMPTY, (uint32_t)((ui - 1) & 1), err, tmo)) break;
+        mbar_arrive_expect_tx(bars + BAR_A_FULL, a_bytes);
+        bulk_load(sA, reinterpret_cast<const unsigned char*>(a.Ahl) + (size_t)rb * a_bytes, a_bytes,
+                  bars + BAR_A_FULL);
+        for (int64_t t = t0; t < t1; ++t, ++s) {
+          const int cb = (int)(s % CB);
+          if (s >= CB && !tc::wait(bars + BAR_C_EMPTY + cb, (uint32_t)(((s / CB) - 1) & 1), err, tmo)) {
+            ok = false;
+            break;
+          }
+          mbar_arrive_expect_tx(bars + BAR_C_FULL + cb, c_bytes);
+          bulk_load(sC + (size_t)cb * c_bytes, reinterpret_cast<const unsigned char*>(a.Bhl) + (size_t)t * c_bytes,
+                    c_bytes, bars + BAR_C_FULL + cb);
         }
-        if (rb == 0) {
-          mbar_arrive_expect_tx(bars + BAR_B_FULL, b_bytes);
-          bulk_load(sB, reinterpret_cast<const unsigned char*>(a.Bhl) + (size_t)tile * b_bytes, b_bytes,
-                    bars + BAR_B_FULL);
-        }
-        const int abuf = (int)(s & 1);
-        if (s >= 2 && !tc::wait(bars + BAR_A_EMPTY + abuf, (uint32_t)(((s - 2) >> 1) & 1), err, tmo)) break;
-        mbar_arrive_expect_tx(bars + BAR_A_FULL + abuf, a_bytes);
-        bulk_load(sA + (size_t)abuf * a_bytes, reinterpret_cast<const unsigned char*>(a.Ahl) + (size_t)rb * a_bytes,
-                  a_bytes, bars + BAR_A_FULL + abuf);
       }
+      // copies still in flight complete before the CTA exits (bounded)
+      for (int64_t d = s > CB ? s - CB : 0; d < s; ++d)
+        mbar_wait_bounded(bars + BAR_C_FULL + (d % CB), (uint32_t)((d / CB) & 1), err, tmo);
+      if (ui > 0) mbar_wait_bounded(bars + BAR_A_FULL, (uint32_t)((ui - 1) & 1), err, tmo);
     }
   } else if (warp == 3) {
     // ---------------------------------------------------------- X producer
-    // X tile of step s: one 2-D tensor copy of rows rb*128.., columns j0..
+    // X tile of step s: one 2-D tensor copy of rows rb*128.., columns t*64..
     // into buffer s % XB (element (row, c) at c*128 + row; rows past ld and
     // columns past N are filled with zeros and count in the bytes)
     if (lane == 0) {
       int64_t s = 0;
-      for (; s < nsteps; ++s) {
-        const int64_t ti = s / a.row_blocks;
-        const int rb = (int)(s % a.row_blocks);
-        const int64_t j0 = (blockIdx.x + ti * gridDim.x) * kTileN;
-        const int xb = (int)(s % XB);
-        if (s >= XB && !tc::wait(bars + BAR_X_EMPTY + xb, (uint32_t)(((s / XB) - 1) & 1), err, tmo)) break;
-        mbar_arrive_expect_tx(bars + BAR_X_FULL + xb, (uint32_t)(kTileM * kTileN * 4));
-        tc::tma_load_2d(sX + (size_t)xb * kTileN * kTileM, &tmX, rb * kTileM, (int)j0, bars + BAR_X_FULL + xb);
+      bool ok = true;
+      for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+        int rb;
+        int64_t t0, t1;
+        rt_unit(a, u, rb, t0, t1);
+        for (int64_t t = t0; t < t1; ++t, ++s) {
+          const int xb = (int)(s % XB);
+          if (s >= XB && !tc::wait(bars + BAR_X_EMPTY + xb, (uint32_t)(((s / XB) - 1) & 1), err, tmo)) {
+            ok = false;
+            break;
+          }
+          mbar_arrive_expect_tx(bars + BAR_X_FULL + xb, (uint32_t)(kTileM * kTileN * 4));
+          tc::tma_load_2d(sX + (size_t)xb * kTileN * kTileM, &tmX, rb * kTileM, (int)(t * kTileN),
+                          bars + BAR_X_FULL + xb);
+        }
       }
       for (int64_t d = s > XB ? s - XB : 0; d < s; ++d)
         mbar_wait_bounded(bars + BAR_X_FULL + (d % XB), (uint32_t)((d / XB) & 1), err, tmo);
@@ -206,51 +233,75 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a, con
     // ----------------------------------------------------------- MMA issue
     if (lane == 0) {
       const uint32_t idesc = tc::instr_desc_bf16(kTileM, kTileN);
-      const uint32_t sA0 = smem_u32(sA), sB0 = smem_u32(sB);
+      const uint32_t sA0 = smem_u32(sA), sC0 = smem_u32(sC);
       const uint32_t sbo = (uint32_t)Kp * 16;      // next 8-row group
-      for (int64_t s = 0; s < nsteps; ++s) {
-        const int rb = (int)(s % a.row_blocks);
-        const int64_t ti = s / a.row_blocks;
-        if (rb == 0 && !tc::wait(bars + BAR_B_FULL, (uint32_t)(ti & 1), err, tmo)) break;
-        const int ab = (int)(s & 1);             // accumulator and A buffer of this step
-        if (!tc::wait(bars + BAR_A_FULL + ab, (uint32_t)((s >> 1) & 1), err, tmo)) break;
-        if (s >= 2 && !tc::wait(bars + BAR_ACC_EMPTY + ab, (uint32_t)(((s - 2) >> 1) & 1), err, tmo)) break;
-        tc::fence_after();
-        const uint32_t d = tmem + (uint32_t)(ab * kTileN);
-        // the NPROD products of the terms, p_i q_j with i + j < NT
-#pragma unroll
-        for (int pr = 0; pr < NPROD; ++pr) {
-          const int ti_a = pr == 2 || pr == 4 ? 1 : (pr == 5 ? 2 : 0);
-          const int ti_b = pr == 1 || pr == 4 ? 1 : (pr == 3 ? 2 : 0);
-          const uint32_t aoff = (uint32_t)ti_a * a_split;
-          const uint32_t boff = (uint32_t)ti_b * b_split;
-          for (int kk = 0; kk < Kp / KSTEP; ++kk) {
-            const uint64_t ad = tc::smem_desc(sA0 + (uint32_t)ab * a_bytes + aoff + (uint32_t)kk * 256u, 128u, sbo);
-            const uint64_t bd = tc::smem_desc(sB0 + boff + (uint32_t)kk * 256u, 128u, sbo);
-            tc::mma_bf16(d, ad, bd, idesc, (pr > 0 || kk > 0) ? 1u : 0u);
+      int64_t s = 0, ui = 0;
+      bool ok = true;
+      for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x, ++ui) {
+        int rb;
+        int64_t t0, t1;
+        rt_unit(a, u, rb, t0, t1);
+        if (!tc::wait(bars + BAR_A_FULL, (uint32_t)(ui & 1), err, tmo)) break;
+        for (int64_t t = t0; t < t1; ++t, ++s) {
+          const int cb = (int)(s % CB), ab = (int)(s & 1);
+          if (!tc::wait(bars + BAR_C_FULL + cb, (uint32_t)((s / CB) & 1), err, tmo) ||
+              (s >= 2 && !tc::wait(bars + BAR_ACC_EMPTY + ab, (uint32_t)(((s - 2) >> 1) & 1), err, tmo))) {
+            ok = false;
+            break;
           }
+          tc::fence_after();
+          const uint32_t d = tmem + (uint32_t)(ab * kTileN);
+          const uint32_t cbase = sC0 + (uint32_t)cb * c_bytes;
+          // the NPROD products of the terms, p_i q_j with i + j < NT
+#pragma unroll
+          for (int pr = 0; pr < NPROD; ++pr) {
+            const int ti_a = pr == 2 || pr == 4 ? 1 : (pr == 5 ? 2 : 0);
+            const int ti_b = pr == 1 || pr == 4 ? 1 : (pr == 3 ? 2 : 0);
+            const uint32_t aoff = (uint32_t)ti_a * a_split;
+            const uint32_t coff = (uint32_t)ti_b * c_split;
+            for (int kk = 0; kk < Kp / KSTEP; ++kk) {
+              const uint64_t ad = tc::smem_desc(sA0 + aoff + (uint32_t)kk * 256u, 128u, sbo);
+              const uint64_t bd = tc::smem_desc(cbase + coff + (uint32_t)kk * 256u, 128u, sbo);
+              tc::mma_bf16(d, ad, bd, idesc, (pr > 0 || kk > 0) ? 1u : 0u);
+            }
+          }
+          tc::mma_commit(bars + BAR_ACC_FULL + ab);
+          tc::mma_commit(bars + BAR_C_EMPTY + cb);
+          mma_steps[0] = (int)(s + 1);
         }
-        tc::mma_commit(bars + BAR_ACC_FULL + ab);
-        tc::mma_commit(bars + BAR_A_EMPTY + ab);
-        *mma_steps = (int)(s + 1);
+        if (!ok) break;
+        tc::mma_commit(bars + BAR_A_EMPTY);     // the unit's block is free once its MMAs are done
       }
     }
   } else if (warp == 2) {
     // ------------------------------------------------------------ store warp
     // Each finished tile of R leaves by one 2-D tensor store; its X buffer is
-    // released once the store has read it.
+    // released once the store has read it.  The wait for a store's read comes
+    // after the next store is issued, so two stores overlap.
     if (lane == 0) {
-      for (int64_t s = 0; s < nsteps; ++s) {
-        const int64_t ti = s / a.row_blocks;
-        const int rb = (int)(s % a.row_blocks);
-        const int64_t j0 = (blockIdx.x + ti * gridDim.x) * kTileN;
-        const int xb = (int)(s % XB);
-        if (!tc::wait(bars + BAR_EPI_DONE + xb, (uint32_t)((s / XB) & 1), err, tmo)) break;
-        tc::tma_store_2d(&tmR, rb * kTileM, (int)j0, sX + (size_t)xb * kTileN * kTileM);
-        tc::bulk_wait_read_all();
-        mbar_arrive(bars + BAR_X_EMPTY + xb);
+      int64_t s = 0;
+      int prev = -1;
+      bool ok = true;
+      for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+        int rb;
+        int64_t t0, t1;
+        rt_unit(a, u, rb, t0, t1);
+        for (int64_t t = t0; t < t1; ++t, ++s) {
+          const int xb = (int)(s % XB);
+          if (!tc::wait(bars + BAR_EPI_DONE + xb, (uint32_t)((s / XB) & 1), err, tmo)) {
+            ok = false;
+            break;
+          }
+          tc::tma_store_2d(&tmR, rb * kTileM, (int)(t * kTileN), sX + (size_t)xb * kTileN * kTileM);
+          if (prev >= 0) {
+            asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+            mbar_arrive(bars + BAR_X_EMPTY + prev);
+          }
+          prev = xb;
+        }
       }
       tc::bulk_wait_all();
+      if (prev >= 0) mbar_arrive(bars + BAR_X_EMPTY + prev);
     }
   } else if (warp >= 4) {
     // ------------------------------------------------------------- epilogue
@@ -272,81 +323,79 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a, con
       named_bar(2, kEpiWarps * 32);
       return f == 0;
     };
-    for (int64_t s = 0; s < nsteps && ok; ++s) {
-      const int64_t ti = s / a.row_blocks;
-      const int rb = (int)(s % a.row_blocks);
-      const int64_t tile = blockIdx.x + ti * gridDim.x;
-      const int64_t j0 = tile * kTileN;
-      const int ab = (int)(s & 1), xb = (int)(s % XB);
+    int64_t s = 0;
+    for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+      int rb;
+      int64_t t0, t1;
+      rt_unit(a, u, rb, t0, t1);
       const int i = rb * kTileM + row_in;
-      const int ncol = (a.N - j0 < kTileN ? (int)(a.N - j0) : kTileN) - c0;
-      // Loads for the partials go out before the waits: this row's running
-      // sum (written by this thread one tile earlier) and c_1 on this half of
-      // the tile, one column per lane.
-      float pold = 0.f, cv = 0.f;
-      if (prow) {
-        if (ti > 0 && i < a.ld) pold = __ldcg(prow + i);
-        if (lane < ncol) cv = __ldg(a.c1 + j0 + c0 + lane);
+      // this row's partial of R c_1^T over the unit's tiles, in tile order
+      float prun = 0.f;
+      for (int64_t t = t0; t < t1 && ok; ++t, ++s) {
+        const int64_t j0 = t * kTileN;
+        const int ab = (int)(s & 1), xb = (int)(s % XB);
+        const int ncol = (a.N - j0 < kTileN ? (int)(a.N - j0) : kTileN) - c0;
+        // c_1 on this half of the tile, one column per lane (loaded before the waits)
+        float cv = 0.f;
+        if (prow && lane < ncol) cv = __ldg(a.c1 + j0 + c0 + lane);
+        ok = tc::wait(bars + BAR_ACC_FULL + ab, (uint32_t)((s >> 1) & 1), err, tmo) &&
+             tc::wait(bars + BAR_X_FULL + xb, (uint32_t)((s / XB) & 1), err, tmo);
+        // the warp-wide tcgen05.ld below needs every lane, so the lanes agree
+        ok = __all_sync(0xffffffffu, ok);
+        tc::fence_after();
+        float d[kTileN / 2];
+#pragma unroll
+        for (int c = 0; c < kTileN / 2; c += 16)
+          tc::tmem_ld<16>(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ab * kTileN + c0 + c), d + c);
+        tc::fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bars + BAR_ACC_EMPTY + ab);
+        float* xs = sX + (size_t)xb * kTileN * kTileM + (size_t)c0 * kTileM + row_in;
+        float s2 = 0.f;
+        // R = X - B C for this thread's row and 32 columns, rounded to the
+        // residual's precision (values past N or ld are cut by the store).
+#pragma unroll
+        for (int c = 0; c < kTileN / 2; ++c) {
+          const float r = xs[c * kTileM] - d[c];
+          d[c] = F32 ? r : __bfloat162float(__float2bfloat16_rn(r));
+          if (c < ncol && i < a.ld) s2 = fmaf(d[c], d[c], s2);
+        }
+        if (prow) {
+          // from the stored (rounded) R as the sweep would read it; c_1 comes
+          // from the lane that loaded it (zero past N)
+#pragma unroll
+          for (int c = 0; c < kTileN / 2; ++c) prun = fmaf(d[c], __shfl_sync(0xffffffffu, cv, c), prun);
+          // ||c_1||^2 over this half of the tile, once per tile (row block 0)
+          if (quarter == 0 && rb == 0) cc1 += (double)cv * (double)cv;
+        }
+        acc2 += (double)s2;
+        // The X buffer now takes the tile of R, which the store warp sends to
+        // global memory by one tensor store: float32 in place (each thread
+        // overwrites only the values it read), bfloat16 packed at the buffer's
+        // start, which overlaps X values of other warps, so for it the warps
+        // first agree that every X value has been read (and whether to go on:
+        // none is left at a named barrier).
+        if (F32) {
+          if (!ok) break;
+#pragma unroll
+          for (int c = 0; c < kTileN / 2; ++c) xs[c * kTileM] = d[c];
+        } else {
+          if (!collective_ok(ok)) {
+            ok = false;
+            break;
+          }
+          __nv_bfloat16* rs = reinterpret_cast<__nv_bfloat16*>(sX + (size_t)xb * kTileN * kTileM) +
+                              (size_t)c0 * kTileM + row_in;
+#pragma unroll
+          for (int c = 0; c < kTileN / 2; ++c) rs[c * kTileM] = __float2bfloat16_rn(d[c]);
+        }
+        fence_proxy_async_shared();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bars + BAR_EPI_DONE + xb);
       }
-      ok = tc::wait(bars + BAR_ACC_FULL + ab, (uint32_t)((s >> 1) & 1), err, tmo) &&
-           tc::wait(bars + BAR_X_FULL + xb, (uint32_t)((s / XB) & 1), err, tmo);
-      // the warp-wide tcgen05.ld below needs every lane, so the lanes agree
-      ok = __all_sync(0xffffffffu, ok);
-      tc::fence_after();
-      float d[kTileN / 2];
-#pragma unroll
-      for (int c = 0; c < kTileN / 2; c += 16)
-        tc::tmem_ld<16>(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ab * kTileN + c0 + c), d + c);
-      tc::fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(bars + BAR_ACC_EMPTY + ab);
-      float* xs = sX + (size_t)xb * kTileN * kTileM + (size_t)c0 * kTileM + row_in;
-      float s2 = 0.f;
-      // R = X - B C for this thread's row and 32 columns, rounded to the
-      // residual's precision (values past N or ld are cut by the store).
-#pragma unroll
-      for (int c = 0; c < kTileN / 2; ++c) {
-        const float r = xs[c * kTileM] - d[c];
-        d[c] = F32 ? r : __bfloat162float(__float2bfloat16_rn(r));
-        if (c < ncol && i < a.ld) s2 = fmaf(d[c], d[c], s2);
-      }
-      if (prow) {
-        // Partial of row i over this CTA's tiles, in tile order, from the
-        // stored (rounded) R as the sweep would read it; c_1 comes from the
-        // lane that loaded it (zero past N).
-        float p1 = 0.f;
-#pragma unroll
-        for (int c = 0; c < kTileN / 2; ++c) p1 = fmaf(d[c], __shfl_sync(0xffffffffu, cv, c), p1);
-        if (ok && i < a.ld) __stcg(prow + i, pold + p1);
-        // ||c_1||^2 over this half of the tile, once per tile (row block 0)
-        if (quarter == 0 && rb == 0) cc1 += (double)cv * (double)cv;
-      }
-      acc2 += (double)s2;
-      // The X buffer now takes the tile of R, which the store warp sends to
-      // global memory by one tensor store: float32 in place (each thread
-      // overwrites only the values it read), bfloat16 packed at the buffer's
-      // start, which overlaps X values of other warps, so for it the warps
-      // first agree that every X value has been read (and whether to go on:
-      // none is left at a named barrier).
-      if (F32) {
-        if (!ok) break;
-#pragma unroll
-        for (int c = 0; c < kTileN / 2; ++c) xs[c * kTileM] = d[c];
-      } else {
-        if (!collective_ok(ok)) break;
-        __nv_bfloat16* rs = reinterpret_cast<__nv_bfloat16*>(sX + (size_t)xb * kTileN * kTileM) +
-                            (size_t)c0 * kTileM + row_in;
-#pragma unroll
-        for (int c = 0; c < kTileN / 2; ++c) rs[c * kTileM] = __float2bfloat16_rn(d[c]);
-      }
-      fence_proxy_async_shared();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(bars + BAR_EPI_DONE + xb);
+      // the unit's part of row i's partial (the rows start at zero)
+      if (ok && prow && i < a.ld) __stcg(prow + i, __ldcg(prow + i) + prun);
     }
-    // A CTA without tiles still owns its partial rows: they are zero.
-    if (prow && ntile_cta == 0)
-      for (int rb = 0; rb < a.row_blocks; ++rb)
-        if (rb * kTileM + row_in < a.ld) __stcg(prow + rb * kTileM + row_in, 0.f);
     if (a.c1 && quarter == 0) {
       cc1 = warp_sum_f64(cc1);
       if (lane == 0) a.CC1[2 * blockIdx.x + half] = cc1;
@@ -356,13 +405,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) refresh_tc_kernel(TcArgs a, con
     if (lane == 0) red[ew] = acc2;
   }
 
-  // Drain: every issued MMA must finish before TMEM is freed.  The last
-  // commit of the MMA thread arrives on BAR_A_EMPTY of its buffer; its phase is waited here
-  // (bounded) by warp 1, then the allocation is released.
+  // Drain: every issued MMA must finish before TMEM is freed.
   __syncthreads();
-  const int issued = *mma_steps;
-  if (warp == 1 && lane == 0 && issued > 0) {
-    mbar_wait_bounded(bars + BAR_A_EMPTY + ((issued - 1) & 1), (uint32_t)(((issued - 1) >> 1) & 1), err, tmo);
+  if (warp == 1 && lane == 0 && mma_steps[0] > 0) {
+    tc::mma_commit(bars + BAR_DRAIN);
+    mbar_wait_bounded(bars + BAR_DRAIN, 0u, err, tmo);
   }
   tc::fence_before();
   __syncthreads();
@@ -506,16 +553,52 @@ static cudaError_t launch_tc(const float* X, void* R, const float* B, const floa
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return cudaErrorInvalidValue;
   }
-  // as many X buffers as shared memory holds beside the operand tiles
+  // Units of (row block, column range): as many column ranges per row block
+  // as fill whole waves of the grid, every range at least one tile.
+  {
+    int bestQ = 1;
+    double best = -1.0;
+    const int qmax = (int)std::min<int64_t>(col_tiles, std::max(1, 8 * sms / row_blocks + 1));
+    for (int Q = 1; Q <= qmax; ++Q) {
+      const int64_t units = (int64_t)row_blocks * Q;
+      const int64_t w = (units + sms - 1) / sms;
+      const double eff = (double)units / (double)(w * std::min<int64_t>(sms, units)) *
+                         ((double)col_tiles / Q) / (double)((col_tiles + Q - 1) / Q);
+      const double score = eff - (units < sms ? 0.5 * (1.0 - (double)units / sms) : 0.0);
+      if (score > best + 1e-9) {
+        best = score;
+        bestQ = Q;
+      }
+      if (units >= sms && eff >= 0.97) {
+        bestQ = Q;
+        break;
+      }
+    }
+    a.Q = bestQ;
+  }
+  // rings: the deepest X ring, then C-factor ring, that fit beside the unit's block
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  int xb = kMaxXBuf;
-  while (xb > 2 && tc_smem(Kp, NT, xb).total > (size_t)optin) --xb;
-  a.xbufs = xb;
-  const size_t smem = tc_smem(Kp, NT, xb).total;
+  static const int kRings[][2] = {{4, 4}, {4, 3}, {4, 2}, {3, 3}, {3, 2}, {2, 3}, {2, 2}};
+  a.xbufs = 0;
+  for (const auto& r : kRings) {
+    if (r[0] > kMaxXBuf || r[1] > kMaxCBuf) continue;
+    if (tc_smem(Kp, NT, r[0], r[1]).total <= (size_t)optin) {
+      a.xbufs = r[0];
+      a.cbufs = r[1];
+      break;
+    }
+  }
+  if (a.xbufs == 0) return cudaErrorInvalidValue;
+  const size_t smem = tc_smem(Kp, NT, a.xbufs, a.cbufs).total;
   e = cudaFuncSetAttribute(refresh_tc_kernel<F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  // the partial rows of R c_1^T start at zero: a CTA adds only the rows of its units
+  if (P1) {
+    e = cudaMemsetAsync(P1, 0, (size_t)2 * sms * ld * sizeof(float), s);
+    if (e != cudaSuccess) return e;
+  }
   refresh_tc_kernel<F32><<<sms, kTcThreads, smem, s>>>(a, tmX, tmR);
   return cudaGetLastError();
 }
