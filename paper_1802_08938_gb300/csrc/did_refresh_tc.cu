@@ -12,17 +12,20 @@
 //     products; the dropped terms are ~2^-16 relative, far below the bfloat16
 //     rounding of the stored R.
 //
-// Kernel structure (one CTA per SM, persistent over 64-column tiles):
-//   warp 0      producer: TMA bulk copies of the C-factor tile (once per
-//               column tile) and the B-factor row block (from L2; double
-//               buffered, so the next block loads while the MMAs run);
+// Kernel structure (one CTA per SM, persistent over units: a unit is one
+// 128-row block of the B factor against a range of 64-column tiles, the
+// ranges per block chosen so the units fill whole waves of the grid):
+//   warp 0      producer: the unit's B-factor row block by one bulk copy (once
+//               per unit, from L2), and the C-factor tile of every step into
+//               a ring of 2-4 buffers;
 //   warp 3      producer of the 128 x 64 X tiles (one 2-D tensor copy each)
 //               into a ring of as many buffers as shared memory holds (2-4),
 //               so the X reads run ahead of the epilogue;
 //   warp 1      allocates 128 TMEM columns (two 128 x 64 float32 accumulators)
 //               and one elected thread issues the tcgen05.mma instructions;
 //   warp 2      stores each finished tile of R by one 2-D tensor copy and
-//               releases its X buffer once the copy has read it;
+//               releases its X buffer once the copy has read it (the wait
+//               comes after the next store is issued, so two overlap);
 //   warps 4-11  epilogue, two warps per TMEM lane quarter (warp w reads lanes
 //               32 (w % 4).. and columns 32 ((w - 4) / 4)..): tcgen05.ld of the
 //               accumulator, R = X - D (rounded to bfloat16 for that mode)
@@ -30,9 +33,10 @@
 //               2-D tensor copy, and the sum of R^2 accumulated in float64.  When
 //               asked, the epilogue also forms the partials of R c_1^T that
 //               the first b-update of the next sweep needs (one row of
-//               partials per CTA and column half, summed over the CTA's
-//               tiles in order) and ||c_1||^2 per CTA and half, so the sweep
-//               needs no extra read of R after a refresh.
+//               partials per CTA and column half, zeroed by the host; a
+//               thread sums its row over a unit's tiles in order and adds
+//               the unit's sum into the row) and ||c_1||^2 per CTA and half,
+//               so the sweep needs no extra read of R after a refresh.
 // Operands live in global memory pre-split and pre-tiled in the no-swizzle
 // K-major core-matrix layout (8 rows x 16 bytes per core matrix, core matrices
 // along K 128 bytes apart, along M/N Kp*16 bytes apart for bfloat16), so each
