@@ -96,7 +96,8 @@ constexpr uint32_t kTmemCols = 512;
 // shared memory.
 constexpr size_t kMinSmem = 120 * 1024;
 constexpr int kSolveThreads = 256;      // eight warps, one column at a time each
-constexpr int kBThreads = 128;
+constexpr int kBThreads = 256;        // B step: eight lanes per row
+constexpr int kBRows = kBThreads / 8;  // rows per block
 constexpr int kNormPartMax = 1024;
 
 // Element (r, c) of a bfloat16 operand tile in the no-swizzle K-major
@@ -1180,56 +1181,121 @@ __global__ void __launch_bounds__(kTcThreads, 1) update_kernel(UArgs a, const __
 // the update pass's partial rows, then reps passes of the K successive b
 // updates with V = C' C'^T (the delta-b rule of Section 4.2, over all repeats):
 //   b_i := [b_i + (w_i - sum_k V_ik db_k) / V_ii]_+ ,  db = b - b_old.
+// Eight lanes per row, four rows per warp: lane q holds entries i = q + 8 s
+// (s < NS = ceil(K / 8)) of the row's gradient r = w - V db in registers.
+// Step i broadcasts entry i from its lane, every lane forms the same update,
+// and the row's lanes subtract V_mi (change of db_i) from their entries, so
+// r_i is always the current w_i - sum_k V_ik db_k (V is symmetric: row i of V
+// is read contiguously).
 // Y (ld x 2K, column-major) holds [D | B]; B is replaced by B', D by db.
 // Block partials of sum_i db_i[m] W[m,i] in float64.
-__global__ void __launch_bounds__(kBThreads) update_b_kernel(const float* __restrict__ Wp, const float* __restrict__ V,
+template <int NS>
+__global__ void __launch_bounds__(kBThreads, 2) update_b_kernel(const float* __restrict__ Wp, const float* __restrict__ V,
                                                              float* Y, double* part, unsigned long long* degen, int K,
                                                              int KN, int ld, int RB, int Q, int reps) {
   extern __shared__ float Vs[];          // K x K, V_ik at Vs[i*K + k] (V is symmetric)
   for (int idx = threadIdx.x; idx < K * K; idx += blockDim.x) Vs[idx] = V[idx];
   __syncthreads();
   __shared__ double red[kBThreads / 32];
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  double dw = 0.0;
-  if (m < ld) {
-    const int rb = m >> 7, r = m & 127;
-    float w[kMaxK], b0[kMaxK], cur[kMaxK], db[kMaxK];
-    for (int i = 0; i < K; ++i) {
-      double s = 0.0;
-      for (int q = 0; q < Q; ++q) s += (double)Wp[((size_t)(q * RB + rb) * KN + i) * 128 + r];
-      w[i] = (float)s;
-      b0[i] = cur[i] = Y[(size_t)m + (size_t)(K + i) * ld];
-      db[i] = 0.f;
+  const int lane = threadIdx.x & 31, q = lane & 7;
+  const int m = blockIdx.x * kBRows + (threadIdx.x >> 3);
+  const bool valid = m < ld;             // the same for the eight lanes of a row
+  const int rb = m >> 7, r128 = m & 127;
+  float w[NS], b0[NS], cur[NS], db[NS], r[NS];
+#pragma unroll
+  for (int t = 0; t < NS; ++t) {
+    const int i = q + 8 * t;
+    w[t] = b0[t] = 0.f;
+    if (valid && i < K) {
+      double sw = 0.0;
+      for (int qq = 0; qq < Q; ++qq) sw += (double)Wp[((size_t)(qq * RB + rb) * KN + (size_t)i) * 128 + r128];
+      w[t] = (float)sw;
+      b0[t] = Y[(size_t)m + (size_t)(K + i) * ld];
     }
-    for (int rr = 0; rr < reps; ++rr) {
-      for (int i = 0; i < K; ++i) {
-        const int kend = rr == 0 ? i : K;
-        float s = 0.f;
-        for (int k = 0; k < kend; ++k) s = fmaf(Vs[i * K + k], db[k], s);
+    cur[t] = b0[t];
+    db[t] = 0.f;
+    r[t] = w[t];
+  }
+  for (int rr = 0; rr < reps; ++rr) {
+#pragma unroll
+    for (int t = 0; t < NS; ++t) {
+      for (int o = 0; o < 8; ++o) {
+        const int i = 8 * t + o;
+        if (i >= K) break;
+        const float ri = __shfl_sync(0xffffffffu, r[t], o, 8);
+        const float ci = __shfl_sync(0xffffffffu, cur[t], o, 8);
+        const float b0i = __shfl_sync(0xffffffffu, b0[t], o, 8);
+        const float dbi = __shfl_sync(0xffffffffu, db[t], o, 8);
         const float vii = Vs[i * K + i];
+        float delta = 0.f;
         if (vii > 0.f) {
-          const float t = cur[i] + (w[i] - s) / vii;
-          cur[i] = t > 0.f ? t : 0.f;
-          db[i] = cur[i] - b0[i];
-        } else if (m == 0) {
+          const float v = ci + ri / vii;
+          const float nb = v > 0.f ? v : 0.f;
+          const float nd = nb - b0i;
+          delta = nd - dbi;
+          if (q == o) {
+            cur[t] = nb;
+            db[t] = nd;
+          }
+        } else if (m == 0 && q == 0) {
           atomicAdd(degen, 1ull);
+        }
+#pragma unroll
+        for (int u = 0; u < NS; ++u) {
+          const int mm = q + 8 * u;
+          if (mm < K) r[u] = fmaf(-Vs[i * K + mm], delta, r[u]);
         }
       }
     }
-    for (int i = 0; i < K; ++i) {
-      Y[(size_t)m + (size_t)(K + i) * ld] = cur[i];
-      Y[(size_t)m + (size_t)i * ld] = db[i];
-      dw += (double)db[i] * (double)w[i];
+  }
+  double dw = 0.0;
+  if (valid) {
+#pragma unroll
+    for (int t = 0; t < NS; ++t) {
+      const int i = q + 8 * t;
+      if (i < K) {
+        Y[(size_t)m + (size_t)(K + i) * ld] = cur[t];
+        Y[(size_t)m + (size_t)i * ld] = db[t];
+        dw += (double)db[t] * (double)w[t];
+      }
     }
   }
   dw = warp_sum_f64(dw);
-  const int wi = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) red[wi] = dw;
+  const int wi = threadIdx.x >> 5;
+  if (lane == 0) red[wi] = dw;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
-    part[blockIdx.x] = s;
+    double sdw = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) sdw += red[i];
+    part[blockIdx.x] = sdw;
+  }
+}
+
+// The B step instantiated for ceil(K / 8) slots of entries per lane.
+template <int NS>
+cudaError_t launch_update_b_ns(const float* Wp, const float* V, float* Y, double* part, unsigned long long* degen,
+                               int K, int KN, int ld, int RB, int Q, int reps, int nb, cudaStream_t s) {
+  update_b_kernel<NS><<<nb, kBThreads, (size_t)K * K * 4, s>>>(Wp, V, Y, part, degen, K, KN, ld, RB, Q, reps);
+  return cudaGetLastError();
+}
+cudaError_t launch_update_b(const float* Wp, const float* V, float* Y, double* part, unsigned long long* degen, int K,
+                            int KN, int ld, int RB, int Q, int reps, int nb, cudaStream_t s) {
+  switch ((K + 7) / 8) {
+#define DID_UB(n) \
+  case n: return launch_update_b_ns<n>(Wp, V, Y, part, degen, K, KN, ld, RB, Q, reps, nb, s);
+    DID_UB(1) DID_UB(2) DID_UB(3) DID_UB(4) DID_UB(5) DID_UB(6) DID_UB(7) DID_UB(8)
+#undef DID_UB
+    default: return cudaErrorInvalidValue;
+  }
+}
+cudaError_t set_update_b_smem(int K) {
+  const int smem = K * K * 4;
+  switch ((K + 7) / 8) {
+#define DID_UB(n) \
+  case n: return cudaFuncSetAttribute(update_b_kernel<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    DID_UB(1) DID_UB(2) DID_UB(3) DID_UB(4) DID_UB(5) DID_UB(6) DID_UB(7) DID_UB(8)
+#undef DID_UB
+    default: return cudaErrorInvalidValue;
   }
 }
 
@@ -1348,7 +1414,7 @@ static WsLayout ws_layout(const BPlan& P) {
   L.V = o;      o += al((size_t)P.K * P.K * 4);
   L.YY = o;     o += al((size_t)4 * P.K * P.K * 4);
   L.Vp = o;     o += al((size_t)P.sgrid * P.npairs * 8);
-  L.part_b = o; o += al((size_t)((P.ld + kBThreads - 1) / kBThreads) * 8);
+  L.part_b = o; o += al((size_t)((P.ld + kBRows - 1) / kBRows) * 8);
   L.part_n = o; o += al((size_t)kNormPartMax * 8);
   L.state = o;  o += al(2 * 8);
   L.err = o;    o += al(16);
@@ -1382,7 +1448,7 @@ BatchedState* batched_create(void* ws, int ld, int64_t N, int K, cudaStream_t s)
   b->part_n = (double*)(p + L.part_n);
   b->state = (double*)(p + L.state);
   b->err = (int*)(p + L.err);
-  b->nb = (ld + kBThreads - 1) / kBThreads;
+  b->nb = (ld + kBRows - 1) / kBRows;
   // the operand tiles past column N stay zero
   // (the tensor-core kernels' limit is the device maximum, so contexts of
   // different shapes never lower it under one another)
@@ -1394,7 +1460,7 @@ BatchedState* batched_create(void* ws, int ld, int64_t N, int K, cudaStream_t s)
       cudaFuncSetAttribute(update_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess ||
       cudaFuncSetAttribute(update_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess ||
       set_solve_smem(K, b->P.nu) != cudaSuccess ||
-      cudaFuncSetAttribute(update_b_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, K * K * 4) != cudaSuccess) {
+      set_update_b_smem(K) != cudaSuccess) {
     cudaGetLastError();
     delete b;
     return nullptr;
@@ -1516,9 +1582,7 @@ cudaError_t batched_sweep(BatchedState* b, float* R, float* Y, float* C, int ld,
     update_kernel<32><<<P.ugrid, kTcThreads, P.usmem, s>>>(ua, b->tmU);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  update_b_kernel<<<b->nb, kBThreads, (size_t)K * K * 4, s>>>(b->Wp, b->V, Y, b->part_b, degen, K, P.KN, ld, P.RB,
-                                                               P.Q, reps_b);
-  e = cudaGetLastError();
+  e = launch_update_b(b->Wp, b->V, Y, b->part_b, degen, K, P.KN, ld, P.RB, P.Q, reps_b, b->nb, s);
   if (e != cudaSuccess) return e;
   // Y^T Y gives B^T B, B^T D and D^T D for the objective and the next sweep.
   e = launch_yy(b, Y, ld, K, s);
