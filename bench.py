@@ -647,6 +647,15 @@ def main():
                                                        tol=1e-5, max_sweeps=200),
         }
         other_launches += sum(v[a]["gpu_launches"] for v in workloads.values() for a in ("fp32", "bf16r"))
+        if bf16 is not None:
+            # the BF16-R ratio on the configuration its target is quoted on,
+            # beside the same-workload ratio above
+            pw = workloads["salt_10000x500000_k100"]
+            bf16["precision_workload"] = {
+                "workload": pw["workload"], "sweeps": pw["fp32"]["sweeps"],
+                "fp32_sweeps_per_s": pw["fp32"]["value"], "bf16r_sweeps_per_s": pw["bf16r"]["value"],
+                "ratio_vs_fp32": pw["ratio_bf16r_vs_fp32"], "objective_rel_diff": pw["objective_rel_diff"],
+                "note": "same seed and start; the float32 line is the library's default for this shape"}
 
     serving = None
     if not args.no_serve and not args.shape:
