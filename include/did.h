@@ -153,7 +153,7 @@ typedef struct {
     int64_t dense_launches;  /* refresh / objective / scaling passes */
     double dense_kernel_ms;
     int64_t tc_refreshes;    /* refreshes done on the tensor cores */
-    double tc_refresh_ms;    /* their device time (operand split + GEMM) */
+    double tc_refresh_ms;    /* their device time (operand split + the tensor-core pass) */
     int32_t lazy_writeback;  /* 1: the sweep defers the write of R in pairs of k */
     int32_t ring_stages;     /* shared-memory column stages per column group */
     int32_t column_pairs;    /* 1: a column group takes two columns per step of a c-pass */
